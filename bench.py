@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Throughput of GB300-native ABEA on the one-launch batch workload.
+
+One step = one pass of the whole hot path (k-mer cache + input checks, band
+loop, end cell, backtrack) over the batch workload "batch_4096_ln5kb":
+4,096 synthetic reads with log-normal lengths (median 5 kb, sigma_ln 0.8,
+clipped to 500 b - 50 kb), k = 6, W = 100.  The metric is band-cell updates
+per second (GCUPS: in-matrix cells filled, summed over reads), also reported
+as reads/s.
+
+  value : device-resident inputs (abea_align_batch_device), CUDA events on
+          the library's stream around K back-to-back steps.
+  e2e   : the same metric through abea_align_packed with page-locked host
+          buffers; each step copies its inputs host->device and its results
+          device->host inside the timed region.
+
+--impl reference runs the CPU oracle (oracle/, FP32) on bounded samples of
+the same workload.  With --gpus N > 1 each rank runs its own replica of the
+workload (reads are independent; there is no data exchange).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch_4096_ln5kb"
+METRIC = "ABEA band-cell updates/s (GCUPS) and reads/s on 1 GB300; p50/p99 latency served"
+UNIT = "GCUPS"
+OPS_PER_CELL = 10   # FP32-pipe ops of the canonical cell: 2 FFMA, 4 FADD, 2 compare, 2 select
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 9]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            try:
+                clk, cmax, util = float(r[1]), float(r[2]), float(r[4])
+            except ValueError:
+                continue
+            mx.append(cmax)
+            if util >= 50:
+                sm.append(clk)
+                for n, v in zip(names, r[6:10]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+        if not sm:
+            sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def oracle_rate(batch, seconds: float, threads: int):
+    """FP32 oracle on a bounded, evenly spaced sample of the batch: (GCUPS, reads/s, sample text)."""
+    from oracle import oracle
+    n = batch.n
+    cells_per_read = (batch.n_events() + batch.n_kmers() + 1).astype(np.float64) * batch.W
+    pilot = batch.subset(np.linspace(0, n - 1, min(n, 2 * threads), dtype=np.int64))
+    t = time.perf_counter()
+    r = oracle.abea_batch(pilot, "f32", n_threads=threads)
+    dt = max(time.perf_counter() - t, 1e-3)
+    rate = r["cells"].sum() / dt
+    want_cells = rate * seconds
+    m = int(np.clip(want_cells / cells_per_read.mean(), threads, n))
+    idx = np.linspace(0, n - 1, m, dtype=np.int64)
+    sample = batch.subset(idx)
+    t = time.perf_counter()
+    r = oracle.abea_batch(sample, "f32", n_threads=threads)
+    dt = time.perf_counter() - t
+    return (float(r["cells"].sum()) / dt / 1e9, m / dt,
+            f"{m} of {n} reads, evenly spaced ({int(r['cells'].sum())} cells), {dt:.1f} s wall")
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2101_05012_gb300 import synth
+    batch = synth.make_batch(args.workload)
+    threads = os.cpu_count() or 1
+    from oracle import oracle
+    oracle.load()
+    step_reads = np.linspace(0, batch.n - 1, 64, dtype=np.int64)
+    sample = batch.subset(step_reads)
+    for _ in range(args.warmup):
+        oracle.abea_batch(sample, "f32", n_threads=threads)
+    times, cells = [], 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle.abea_batch(sample, "f32", n_threads=threads)
+        times.append(time.perf_counter() - t)
+        cells = int(r["cells"].sum())
+    total = sum(times)
+    value = cells * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "reads": batch.n, "W": batch.W, "k": batch.k,
+                       "step": "FP32 CPU oracle over 64 evenly spaced reads of the workload"},
+            "reads_per_s": 64 * args.steps / total,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"64 of {batch.n} reads per step, {cells} cells"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2101_05012_gb300 import binding, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    batch = synth.make_batch(args.workload)
+    n = batch.n
+    ctx = binding.Context(local_rank)
+    ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
+    pair_off = binding.pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
+
+    # device-resident inputs and outputs
+    d_seq = torch.from_numpy(batch.seq).to(dev)
+    d_ev = torch.from_numpy(batch.events).to(dev)
+    d_out = torch.zeros(n * 24, dtype=torch.uint8, device=dev)
+    d_pairs = torch.zeros(int(pair_off[-1]) * 2, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step():
+        ctx.align_batch_device(n, batch.W, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out,
+                               d_pairs, pair_off, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    res = binding.results_from_bytes(d_out.cpu().numpy())
+    if not np.all(res["status"] == 0):
+        raise SystemExit(f"bench: {int(np.sum(res['status'] != 0))} reads failed")
+    cells = int(res["cells"].sum())
+    ctx.last_launch_stats()                      # reset the launch counters
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    launches, align_ms = ctx.last_launch_stats()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * cells * args.steps / (ms_total / 1e3) / 1e9
+    reads_per_s = world * n * args.steps / (ms_total / 1e3)
+
+    # end to end through the host-memory call, page-locked host buffers
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    h_seq, h_ev = pin(batch.seq), pin(batch.events)
+    h_out = torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy()
+    h_pairs = torch.zeros(int(pair_off[-1]) * 2, dtype=torch.int32).pin_memory().numpy()
+    import ctypes
+    sc = np.ascontiguousarray(batch.scalings, np.float32)
+
+    def e2e_step():
+        rc = ctx.lib.abea_align_packed(ctx.h, n, batch.W, binding._p(h_seq), binding._p(batch.seq_off),
+                                       binding._p(h_ev), binding._p(batch.ev_off), binding._p(sc),
+                                       binding._p(h_out), binding._p(h_pairs), binding._p(pair_off),
+                                       ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise binding.AbeaError(rc, "abea_align_packed")
+
+    e2e_step()
+    ctx.last_launch_stats()
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t
+    e2e_launches, _ = ctx.last_launch_stats()
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    r2 = binding.results_from_bytes(h_out)
+    if not np.array_equal(r2, res):
+        raise SystemExit("bench: host-memory results differ from device-resident results")
+    e2e_value = world * cells * e2e_steps / e2e_s / 1e9
+    h2d = int(batch.seq.nbytes + batch.events.nbytes + n * (112 + 4))
+    d2h = int(n * 24 + (pair_off[-1] - pair_off[0]) * 8)
+
+    # roofline of the core kernel: FP32-pipe issue
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    align_ms_launch = align_ms / max(args.steps, 1)
+    achieved = cells * OPS_PER_CELL / (align_ms_launch / 1e3) / 1e12
+    peak = sms * 128 * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "align_kernel<4,false>", "per_launch_ms": align_ms_launch,
+                "ops_per_cell": OPS_PER_CELL,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)"}
+    if clk and clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        gc, rps, desc = oracle_rate(batch, args.cpu_seconds, threads)
+        cpu = {"value": gc, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "reads_per_s": rps}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "reads": n, "W": batch.W, "k": batch.k,
+                           "cells_per_step": cells, "bases_per_step": int(batch.seq.size),
+                           "events_per_step": int(batch.events.size),
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "l2": "inputs (195 MB events) and outputs (2.4 GB trace per step) exceed the 129 MB L2"},
+                "reads_per_s": reads_per_s, "kernel_gcups": cells / (align_ms_launch / 1e3) / 1e9,
+                "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,155 @@
+/*
+ * abea.h -- C ABI of the GB300-native Adaptive Banded Event Alignment library.
+ *
+ * The problem (H. Gamaarachchi, PhD thesis, UNSW 2020, Ch.5, Alg.
+ * adaptivebandedcpu): given a read's base sequence `ref`, a k-mer pore model
+ * and the read's detected events, align the events to the read's k-mers with
+ * an adaptively banded dynamic program and return the alignment as a list of
+ * {event index, k-mer index} pairs.  The library adds the per-read score of
+ * that alignment.
+ *
+ * Conventions shared by every call:
+ *   - Return value: ABEA_OK (0) or a negative ABEA_ERR_* code; no exception
+ *     crosses the ABI.  abea_strerror() names a code.
+ *   - Per-read outcome: abea_result.status, one of ABEA_READ_*.
+ *   - Host pointers are owned by the caller and only read (or, for outputs,
+ *     written) during the call.  Device pointers (the *_device call) are
+ *     borrowed for the duration of the call's work on the given stream.
+ *   - The context owns every device allocation it makes; it copies the model.
+ *     A context is not thread-safe: use one context per host thread.
+ *   - Indices are 0-based.  Pairs are (event, k-mer) int32 pairs in
+ *     ascending order.  A k-mer's model row is its rank over A,C,G,T with
+ *     the first base most significant (A=0, C=1, G=2, T=3).
+ *   - Band width W: 2 <= W <= 256.
+ *   - Scores are FP32.  Events are FP32 event means in pA (the thesis's
+ *     Alg. adaptivebandedcpucomputelog uses only the mean of an event).
+ */
+#ifndef ABEA_H
+#define ABEA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define ABEA_OK 0
+#define ABEA_ERR_ARG (-1)        /* invalid argument (null pointer, bad size, W out of range, k mismatch) */
+#define ABEA_ERR_CAPACITY (-2)   /* an output buffer is too small (abea_align: required pairs in out->n_pairs) */
+#define ABEA_ERR_NOMEM (-3)      /* a device or pinned-host allocation failed, or the memory budget is too small */
+#define ABEA_ERR_CUDA (-4)       /* a CUDA runtime call failed */
+#define ABEA_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+#define ABEA_ERR_NO_MODEL (-6)   /* no pore model set */
+
+/* Per-read status. */
+#define ABEA_READ_OK 0           /* aligned */
+#define ABEA_READ_FAIL_NO_END 1  /* no band reached the last k-mer with a finite score */
+#define ABEA_READ_BAD_INPUT 2    /* non-ACGT base, non-finite event, var <= 0, no events, or seq shorter than k */
+#define ABEA_READ_CAPACITY 3     /* the read's pair capacity is smaller than its alignment (n_pairs = required) */
+
+typedef struct abea_ctx abea_ctx;
+
+/* Read-model scaling (thesis Sec. ABEA, "read-model scaling"): the model
+ * mean of every k-mer becomes mean*scale + shift; its stdv becomes
+ * stdv*var.  var = 1 is the thesis's two-parameter scaling exactly. */
+typedef struct {
+    float scale, shift, var;
+} abea_scalings;
+
+/* One read on the host: event means, bases ('A','C','G','T'), scalings.
+ * n_kmers = seq_len - k + 1. */
+typedef struct {
+    const float *ev_mean;
+    int32_t n_events;
+    const char *seq;
+    int32_t seq_len;
+    abea_scalings sc;
+} abea_read;
+
+/* Per-read result.
+ * score  : FP32 score of the alignment: the best S(e, n_k-1) + (n_e-1-e)*ln(1/100),
+ *          -inf when status != OK.
+ * e_end  : event of that end cell.
+ * cells  : in-matrix band cells filled for this read (the throughput unit). */
+typedef struct {
+    float score;
+    int32_t status;
+    int32_t n_pairs;
+    int32_t e_end;
+    int64_t cells;
+} abea_result;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the
+ * device memory the context may hold for batch work (0 = 90 % of the free
+ * memory at creation).  Batches whose working set exceeds the budget are
+ * run in several waves that reuse the same buffers (thesis Sec. "Heuristic
+ * based memory pre-allocation": memory is allocated once and reused).
+ * On error *ctx is NULL. */
+int abea_create(abea_ctx **ctx, int device, size_t mem_budget_bytes);
+
+/* Release every device and pinned allocation of the context. NULL is a no-op. */
+void abea_destroy(abea_ctx *ctx);
+
+/* Human-readable name of a return code. */
+const char *abea_strerror(int code);
+
+/* Set the pore model (thesis Sec. "Methylation calling": a table of all 4^k
+ * k-mers with a mean level and a standard deviation).  level_mean and
+ * level_stdv are host arrays of 4^k floats, copied.  1 <= k <= 12; every
+ * stdv must be finite and > 0 and every mean finite (else ABEA_ERR_ARG). */
+int abea_set_model(abea_ctx *ctx, int k, const float *level_mean, const float *level_stdv);
+
+/* Align one read, synchronously.  pairs: host int32[2*cap].  If the
+ * alignment has more than cap pairs, returns ABEA_ERR_CAPACITY with the
+ * required count in out->n_pairs.  cap = n_events + n_kmers - 1 always
+ * suffices. */
+int abea_align(abea_ctx *ctx, const abea_read *read, int W, abea_result *out,
+               int32_t *pairs, int32_t cap);
+
+/* Align n reads given as abea_read records (host memory).  out: host
+ * abea_result[n].  pairs: host int32[2*pair_off[n]]; read i's pairs go to
+ * pairs[2*pair_off[i] .. 2*pair_off[i+1]) and its capacity is
+ * pair_off[i+1]-pair_off[i] pairs.  Host-to-device copies, kernels and the
+ * device-to-host copy are issued on cuda_stream (a cudaStream_t, or NULL for
+ * the context's own stream); the call returns after the results are on the
+ * host. */
+int abea_align_batch(abea_ctx *ctx, const abea_read *reads, int32_t n, int W,
+                     abea_result *out, int32_t *pairs, const int64_t *pair_off, void *cuda_stream);
+
+/* As abea_align_batch, with the reads packed on the host as structures of
+ * arrays: read i's bases are seq[seq_off[i] .. seq_off[i+1]), its events
+ * events[ev_off[i] .. ev_off[i+1]), its scalings sc[i]. */
+int abea_align_packed(abea_ctx *ctx, int32_t n, int W,
+                      const char *seq, const int64_t *seq_off,
+                      const float *events, const int64_t *ev_off, const abea_scalings *sc,
+                      abea_result *out, int32_t *pairs, const int64_t *pair_off, void *cuda_stream);
+
+/* Align n reads whose bulk data is already in device memory.  The offsets
+ * and scalings are host arrays (as in abea_align_packed); d_seq (bases),
+ * d_events, d_out (abea_result[n]) and d_pairs (int32[2*pair_off[n]]) are
+ * device pointers.  All work is enqueued on cuda_stream and the call
+ * returns without waiting for it; the outputs are valid once the stream
+ * reaches that point.  The batch must fit the memory budget in one wave
+ * (else ABEA_ERR_NOMEM). */
+int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
+                            const uint8_t *d_seq, const int64_t *seq_off,
+                            const float *d_events, const int64_t *ev_off, const abea_scalings *sc,
+                            abea_result *d_out, int32_t *d_pairs, const int64_t *pair_off,
+                            void *cuda_stream);
+
+/* Launch statistics accumulated since the previous call of this function
+ * (or since the context was created): the number of kernel launches the
+ * batch calls issued, and the summed device time of their core-kernel
+ * launches in milliseconds, measured with CUDA events recorded on each
+ * call's stream immediately around the core kernel.  Waits for those events;
+ * then resets both counters.  Up to 4096 core-kernel launches are timed
+ * between two calls (later ones are folded into the last slot). */
+int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABEA_H */

@@ -54,6 +54,16 @@ typedef double real;
 #define TR_U 1
 #define TR_L 2
 
+/* FP32 only: every RENORM_PERIOD bands, while the band and the one before
+ * lie wholly in the matrix, all their scores are shifted up by R, a multiple
+ * of 1024 no larger in magnitude than their maximum (reading A13).  The
+ * shift is exact (each difference is representable), so it changes no
+ * decision by itself; it keeps the running scores small, so that later FP32
+ * additions round at a fine ulp instead of drifting on long reads.  The
+ * shift applied so far is carried in FP64 and added back to the end score. */
+#define RENORM_PERIOD 64
+#define RENORM_BELOW (-2048.0f)
+
 /* ln(1/sqrt(2*pi)) and sqrt(1/2), to 20 digits. */
 #define LOG_INV_SQRT_2PI (-0.91893853320467274178)
 #define SQRT_HALF 0.70710678118654752440
@@ -319,6 +329,13 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
 #endif
     }
     double min_margin = INFINITY;
+    double *band_frame = (double *)calloc((size_t)n_bands, sizeof(double));   /* shift of each band's scores */
+    double frame = 0.0;
+    if (!band_frame) { res->status = ST_NOMEM; free(S); free(T); free(ll_e); free(ll_k);
+#ifndef ORACLE_F32
+        free(M);
+#endif
+        free_read(&p, ranks); return ST_NOMEM; }
 
     /* Band b holds the cells with e + k = b - 2; offset j of band b is the
      * cell (ll_e[b] - j, ll_k[b] + j).  Offset 0 is the band's max-event end,
@@ -394,17 +411,36 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
             TRACE(b, j) = dir;
             res->cells++;
         }
+#ifdef ORACLE_F32
+        if (b % RENORM_PERIOD == 0 && ll_e[b - 1] >= W - 1 && ll_k[b - 1] >= 0 &&
+            ll_e[b - 1] + 1 < n_e && ll_k[b - 1] + W + 1 < n_k) {
+            float top = -INFINITY;
+            for (int32_t j = 0; j < W; j++) {
+                top = fmaxf(top, SCORE(b, j));
+                top = fmaxf(top, SCORE(b - 1, j));
+            }
+            if (top <= RENORM_BELOW) {
+                float R = -1024.0f * floorf(-top / 1024.0f);
+                for (int32_t j = 0; j < W; j++) {
+                    SCORE(b, j) -= R;
+                    SCORE(b - 1, j) -= R;
+                }
+                frame += (double)R;
+            }
+        }
+#endif
+        band_frame[b] = frame;
     }
 
     /* end cell (A12): over events e, the cell (e, n_k-1) in band e+n_k+1;
      * the remaining n_e-1-e events are trimmed at lp_trim each. */
-    real best = -INFINITY, second = -INFINITY;
+    double best = -INFINITY, second = -INFINITY;
     int32_t e_best = -1;
     for (int32_t e = 0; e < n_e; e++) {
         int64_t b = (int64_t)e + n_k + 1;
         int32_t j = ll_e[b] - e;
         if (j < 0 || j >= W) continue;
-        real cand = SCORE(b, j) + (real)(n_e - 1 - e) * p.lp_trim;
+        double cand = band_frame[b] + (double)(SCORE(b, j) + (real)(n_e - 1 - e) * p.lp_trim);
         if (cand > best) { second = best; best = cand; e_best = e; }
         else if (cand > second) second = cand;
     }
@@ -412,7 +448,7 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
     if (best != -INFINITY && second != -INFINITY && best - second < min_margin)
         min_margin = best - second;
 #endif
-    res->score = best;
+    res->score = (double)(real)best;
     res->e_end = e_best;
 
     if (best == -INFINITY) {
@@ -460,6 +496,7 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
     if (band_scores) memcpy(band_scores, S, sizeof(real) * (size_t)(n_bands * W));
 #undef SCORE
 #undef TRACE
+    free(band_frame);
     free(S); free(T); free(ll_e); free(ll_k);
 #ifndef ORACLE_F32
     free(M);

@@ -1,0 +1,208 @@
+"""Python binding of libabea (include/abea.h): argument marshalling only.
+
+Every step of the alignment runs in the library's CUDA kernels; this module
+converts numpy arrays / torch tensors into the pointers and sizes of the C
+ABI and back.  It never falls back to a CPU path: if the library cannot be
+loaded, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+ABEA_OK = 0
+ABEA_ERR_ARG = -1
+ABEA_ERR_CAPACITY = -2
+ABEA_ERR_NOMEM = -3
+ABEA_ERR_CUDA = -4
+ABEA_ERR_TIMEOUT = -5
+ABEA_ERR_NO_MODEL = -6
+
+READ_OK, READ_FAIL_NO_END, READ_BAD_INPUT, READ_CAPACITY = range(4)
+
+# the functions include/abea.h declares
+EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
+           "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats"]
+
+
+class Scalings(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_float), ("shift", ctypes.c_float), ("var", ctypes.c_float)]
+
+
+class Read(ctypes.Structure):
+    _fields_ = [("ev_mean", ctypes.c_void_p), ("n_events", ctypes.c_int32), ("seq", ctypes.c_void_p),
+                ("seq_len", ctypes.c_int32), ("sc", Scalings)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_float), ("status", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
+                ("e_end", ctypes.c_int32), ("cells", ctypes.c_int64)]
+
+
+RESULT_DTYPE = np.dtype([("score", "<f4"), ("status", "<i4"), ("n_pairs", "<i4"), ("e_end", "<i4"),
+                         ("cells", "<i8")])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result) == 24
+
+_lib = None
+
+
+class AbeaError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        name = load().abea_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {name} ({code})")
+
+
+def load(path: Optional[str] = None):
+    """Open libabea.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if path is None and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libabea.so not found at {p}: the CUDA extension is required")
+    lib = ctypes.CDLL(p)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.abea_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t]
+    lib.abea_destroy.argtypes = [P]
+    lib.abea_destroy.restype = None
+    lib.abea_strerror.argtypes = [ctypes.c_int]
+    lib.abea_strerror.restype = ctypes.c_char_p
+    lib.abea_set_model.argtypes = [P, ctypes.c_int, P, P]
+    lib.abea_align.argtypes = [P, ctypes.POINTER(Read), ctypes.c_int, ctypes.POINTER(Result), P, i32]
+    lib.abea_align_batch.argtypes = [P, P, i32, ctypes.c_int, P, P, P, P]
+    lib.abea_align_packed.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+    lib.abea_align_batch_device.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+    lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    for f in EXPORTS:
+        if f not in ("abea_destroy", "abea_strerror"):
+            getattr(lib, f).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != ABEA_OK:
+        raise AbeaError(rc, what)
+
+
+def pair_offsets(n_events: np.ndarray, n_kmers: np.ndarray) -> np.ndarray:
+    """Pair capacity n_e + n_k - 1 per read (always enough), as offsets."""
+    cap = np.maximum(np.asarray(n_events, np.int64) + np.asarray(n_kmers, np.int64) - 1, 1)
+    off = np.zeros(len(cap) + 1, np.int64)
+    np.cumsum(cap, out=off[1:])
+    return off
+
+
+class Context:
+    """An abea_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.abea_create(ctypes.byref(h), device, mem_budget_bytes), "abea_create")
+        self.h = h
+        self.k = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.abea_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_model(self, k: int, level_mean, level_stdv):
+        m = np.ascontiguousarray(level_mean, np.float32)
+        s = np.ascontiguousarray(level_stdv, np.float32)
+        if m.size != 4 ** k or s.size != 4 ** k:
+            raise ValueError("model arrays must hold 4^k entries")
+        _check(self.lib.abea_set_model(self.h, k, _p(m), _p(s)), "abea_set_model")
+        self.k = k
+
+    def align(self, events, seq, scalings, W: int):
+        """One read (abea_align).  Returns (result dict, pairs int32[n,2])."""
+        ev = np.ascontiguousarray(events, np.float32)
+        sq = np.frombuffer(seq.encode() if isinstance(seq, str) else bytes(seq), np.uint8).copy()
+        cap = max(len(ev) + len(sq), 1)
+        pairs = np.zeros((cap, 2), np.int32)
+        rd = Read(_p(ev).value, len(ev), _p(sq).value, len(sq), Scalings(*[float(v) for v in scalings]))
+        res = Result()
+        _check(self.lib.abea_align(self.h, ctypes.byref(rd), W, ctypes.byref(res), _p(pairs), cap), "abea_align")
+        out = {f: getattr(res, f) for f, _ in Result._fields_}
+        return out, pairs[:res.n_pairs].copy() if res.status == READ_OK else pairs[:0]
+
+    def align_batch(self, events_list, seqs, scalings, W: int, stream=None):
+        """abea_align_batch over lists of reads.  Returns (results, pairs, pair_off)."""
+        n = len(events_list)
+        evs = [np.ascontiguousarray(e, np.float32) for e in events_list]
+        sqs = [np.frombuffer(s.encode() if isinstance(s, str) else bytes(s), np.uint8).copy() for s in seqs]
+        recs = (Read * max(n, 1))()
+        for i in range(n):
+            sc = scalings[i]
+            recs[i] = Read(_p(evs[i]).value if len(evs[i]) else None, len(evs[i]),
+                           _p(sqs[i]).value if len(sqs[i]) else None, len(sqs[i]),
+                           Scalings(float(sc[0]), float(sc[1]), float(sc[2])))
+        n_k = np.array([len(s) for s in sqs], np.int64) - (self.k or 1) + 1
+        pair_off = pair_offsets([len(e) for e in evs], np.maximum(n_k, 1))
+        out = np.zeros(n, RESULT_DTYPE)
+        pairs = np.zeros((max(int(pair_off[-1]), 1), 2), np.int32)
+        _check(self.lib.abea_align_batch(self.h, ctypes.cast(recs, ctypes.c_void_p), n, W, _p(out), _p(pairs),
+                                         _p(pair_off), ctypes.c_void_p(stream)), "abea_align_batch")
+        return out, pairs, pair_off
+
+    def align_packed(self, batch, W: Optional[int] = None, stream=None, pair_off=None):
+        """abea_align_packed over a synth.Batch (host arrays).  Returns (results, pairs, pair_off)."""
+        W = batch.W if W is None else W
+        n = batch.n
+        if pair_off is None:
+            pair_off = pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
+        out = np.zeros(n, RESULT_DTYPE)
+        pairs = np.zeros((max(int(pair_off[-1]), 1), 2), np.int32)
+        sc = np.ascontiguousarray(batch.scalings, np.float32)
+        _check(self.lib.abea_align_packed(self.h, n, W, _p(batch.seq), _p(batch.seq_off), _p(batch.events),
+                                          _p(batch.ev_off), _p(sc), _p(out), _p(pairs), _p(pair_off),
+                                          ctypes.c_void_p(stream)), "abea_align_packed")
+        return out, pairs, pair_off
+
+    def align_batch_device(self, n: int, W: int, d_seq, seq_off, d_events, ev_off, scalings, d_out, d_pairs,
+                           pair_off, stream=None):
+        """abea_align_batch_device: d_* are torch CUDA tensors (uint8 bases, float32 events,
+        uint8[n*24] results, int32 pairs); offsets and scalings are host numpy arrays."""
+        sc = np.ascontiguousarray(scalings, np.float32)
+        so = np.ascontiguousarray(seq_off, np.int64)
+        eo = np.ascontiguousarray(ev_off, np.int64)
+        po = np.ascontiguousarray(pair_off, np.int64)
+        _check(self.lib.abea_align_batch_device(
+            self.h, n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
+            _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
+            ctypes.c_void_p(stream)), "abea_align_batch_device")
+
+    def last_launch_stats(self):
+        n = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(self.lib.abea_last_launch_stats(self.h, ctypes.byref(n), ctypes.byref(ms)), "abea_last_launch_stats")
+        return n.value, ms.value
+
+
+def results_from_bytes(buf: np.ndarray) -> np.ndarray:
+    """View a uint8 buffer of n*24 bytes (device results copied back) as results."""
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), RESULT_DTYPE)

@@ -1,0 +1,651 @@
+// Host side of libabea: the C ABI of include/abea.h.
+//
+// A batch call (thesis Alg. a:exec and Alg. a:memalloc) serialises the reads
+// into flat arrays with per-read offsets (Sec. "Data array serialisation"),
+// copies them to the device, runs the pre-kernel (k-mer cache, input checks)
+// and the core kernel (band loop, end cell, backtrack), and copies the
+// results back.  Device buffers are allocated once per context and reused,
+// growing only when a batch needs more (Sec. "Heuristic based memory
+// pre-allocation"); when a batch needs more than the context's memory budget
+// it is split into waves that reuse the same buffers.  Unlike the thesis,
+// no read is sent to the CPU: reads are processed longest first by a
+// persistent kernel, which takes the place of the CPU/GPU split of
+// Sec. "Heterogeneous processing".
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "abea_internal.h"
+
+using abea::AlignArgs;
+using abea::Geometry;
+using abea::ModelRow;
+using abea::ReadDesc;
+
+namespace {
+
+constexpr double kLogInvSqrt2Pi = -0.91893853320467274178;   // ln(1/sqrt(2 pi))
+constexpr double kSqrtHalf = 0.70710678118654752440;         // sqrt(1/2)
+constexpr int kMaxTimed = 4096;                              // timed launches kept between stats calls
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct abea_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    size_t budget = 0;
+    size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
+    int k = 0;
+    DevBuf model;
+    DevBuf rd, order, flags, kc, trace, lle, queue;
+    DevBuf events, seq, res, pairs;   // staging of the host-memory calls
+    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs;
+    cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
+    std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
+    int32_t n_timed = 0;                        // pairs recorded since the last stats call
+    int32_t last_launches = 0;                  // kernel launches since the last stats call
+    int grid[9][2] = {};
+};
+
+namespace {
+
+int cuda_err(cudaError_t e)
+{
+    if (e == cudaSuccess) return ABEA_OK;
+    cudaGetLastError();
+    return ABEA_ERR_CUDA;
+}
+
+int ensure_dev(abea_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return ABEA_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 4);
+    want = (want + 255) & ~size_t(255);
+    if (b.p) {
+        cudaFree(b.p);
+        c->held -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return ABEA_ERR_NOMEM;
+        }
+        want = bytes;
+    }
+    b.cap = want;
+    c->held += want;
+    return ABEA_OK;
+}
+
+int ensure_host(HostBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return ABEA_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 4);
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    if (cudaMallocHost(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return ABEA_ERR_NOMEM;
+    }
+    b.cap = want;
+    return ABEA_OK;
+}
+
+void free_dev(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+void free_host(HostBuf &b)
+{
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+cudaStream_t pick_stream(abea_ctx *c, void *s) { return s ? (cudaStream_t)s : c->own_stream; }
+
+// Per-read footprint in device memory (k-mer cache entries, trace words, ll_e records).
+struct Footprint {
+    size_t kc, trace, lle;
+};
+
+Footprint footprint(int64_t n_e, int64_t n_k, const Geometry &g)
+{
+    const int64_t bands = n_e + n_k + 1;
+    Footprint f;
+    f.kc = (size_t)std::max<int64_t>(n_k, 0);
+    f.trace = (size_t)(bands * g.rec_words);
+    f.lle = (size_t)((bands + 3) / 4 * 4);
+    return f;
+}
+
+// Build the descriptors of reads `ids` (indices into the caller's arrays).
+// ev_base/seq_base: offsets of the first event/base of each read in the
+// arrays the kernels will read; pair_base/pair_cap likewise for the pairs.
+int plan_reads(const abea_ctx *c, const Geometry &g, const std::vector<int32_t> &ids,
+               const int64_t *seq_off, const int64_t *ev_off, const abea_scalings *sc,
+               const std::vector<int64_t> &seq_base, const std::vector<int64_t> &ev_base,
+               const std::vector<int64_t> &pair_base, const std::vector<int32_t> &pair_cap,
+               ReadDesc *rd, int32_t *order, Footprint &total)
+{
+    total = Footprint{0, 0, 0};
+    const size_t n = ids.size();
+    for (size_t t = 0; t < n; t++) {
+        const int32_t i = ids[t];
+        const int64_t n_e = ev_off[i + 1] - ev_off[i];
+        const int64_t seq_len = seq_off[i + 1] - seq_off[i];
+        const int64_t n_k = seq_len - c->k + 1;
+        ReadDesc d;
+        std::memset(&d, 0, sizeof(d));
+        const abea_scalings s = sc[i];
+        bool bad = n_e < 1 || n_k < 1 || n_e > (1LL << 30) || n_k > (1LL << 30) ||
+                   !std::isfinite(s.scale) || !std::isfinite(s.shift) || !std::isfinite(s.var) || !(s.var > 0.0f);
+        d.ev_off = ev_base[t];
+        d.seq_off = seq_base[t];
+        d.pair_off = pair_base[t];
+        d.pair_cap = pair_cap[t];
+        d.host_bad = bad ? 1 : 0;
+        if (!bad) {
+            d.n_e = (int32_t)n_e;
+            d.n_k = (int32_t)n_k;
+            // transition constants (thesis Alg. adaptivebandedcpucompute), FP64 then rounded once
+            const double epk = (double)n_e / (double)n_k;
+            const double lp_skip = std::log(1e-10);
+            const double lp_stay = std::log(1.0 - 1.0 / (epk + 1.0));
+            const double lp_step = std::log(1.0 - std::exp(lp_skip) - std::exp(lp_stay));
+            const double lp_trim = std::log(1.0 / 100.0);
+            d.lp_skip = (float)lp_skip;
+            d.lp_stay = (float)lp_stay;
+            d.lp_step = (float)lp_step;
+            d.lp_trim = (float)lp_trim;
+            d.scale = (double)s.scale;
+            d.shift = (double)s.shift;
+            d.inv_var = 1.0 / (double)s.var;
+            d.log_var = std::log((double)s.var);
+            const Footprint f = footprint(n_e, n_k, g);
+            d.kc_off = (int64_t)total.kc;
+            d.tr_off = (int64_t)total.trace;
+            d.ll_off = (int64_t)total.lle;
+            total.kc += f.kc;
+            total.trace += f.trace;
+            total.lle += f.lle;
+        }
+        rd[t] = d;
+    }
+    // longest reads first; host-rejected reads last
+    std::vector<int64_t> key(n);
+    for (size_t t = 0; t < n; t++) key[t] = rd[t].host_bad ? -1 : (int64_t)rd[t].n_e + rd[t].n_k;
+    std::vector<int32_t> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return key[a] > key[b]; });
+    std::memcpy(order, ord.data(), n * sizeof(int32_t));
+    return ABEA_OK;
+}
+
+// Device bytes one wave of `n` reads holds besides its inputs/outputs.
+size_t work_bytes(size_t n, const Footprint &f)
+{
+    return n * (sizeof(ReadDesc) + 2 * sizeof(int32_t)) + f.kc * 16 + f.trace * 4 + f.lle * 4 + 256;
+}
+
+// Enqueue prep + align for one planned wave whose descriptors/order are in
+// host pinned memory h_rd/h_order and whose inputs/outputs are device arrays.
+int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, const ReadDesc *h_rd,
+             const int32_t *h_order, const uint8_t *d_seq, const float *d_events, abea_result *d_res,
+             int32_t *d_pairs, int W, cudaStream_t st)
+{
+    int rc;
+    if ((rc = ensure_dev(c, c->rd, (size_t)n * sizeof(ReadDesc)))) return rc;
+    if ((rc = ensure_dev(c, c->order, (size_t)n * sizeof(int32_t)))) return rc;
+    if ((rc = ensure_dev(c, c->flags, (size_t)n * sizeof(int32_t)))) return rc;
+    if ((rc = ensure_dev(c, c->kc, std::max<size_t>(f.kc, 1) * 16))) return rc;
+    if ((rc = ensure_dev(c, c->trace, std::max<size_t>(f.trace, 4) * 4))) return rc;
+    if ((rc = ensure_dev(c, c->lle, std::max<size_t>(f.lle, 4) * 4))) return rc;
+    if ((rc = ensure_dev(c, c->queue, 256))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->rd.p, h_rd, (size_t)n * sizeof(ReadDesc), cudaMemcpyHostToDevice, st))))
+        return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->order.p, h_order, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st))))
+        return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
+    if ((rc = cuda_err(cudaMemsetAsync(c->queue.p, 0, sizeof(int32_t), st)))) return rc;
+    if ((rc = cuda_err((cudaError_t)abea::launch_prep((const ReadDesc *)c->rd.p, n, d_seq, d_events,
+                                                       (const ModelRow *)c->model.p, c->k, (float4 *)c->kc.p,
+                                                       (int32_t *)c->flags.p, st))))
+        return rc;
+    c->last_launches++;
+    int &grid = c->grid[g.C][g.mixed ? 1 : 0];
+    if (grid <= 0) grid = abea::align_grid_size(g.C, g.mixed, c->device);
+    if (grid <= 0) return ABEA_ERR_CUDA;
+    AlignArgs a;
+    a.rd = (const ReadDesc *)c->rd.p;
+    a.order = (const int32_t *)c->order.p;
+    a.flags = (const int32_t *)c->flags.p;
+    a.n = n;
+    a.W = W;
+    a.L = g.L;
+    a.events = d_events;
+    a.seq = d_seq;
+    a.kc = (const float4 *)c->kc.p;
+    a.trace = (uint32_t *)c->trace.p;
+    a.lle = (int32_t *)c->lle.p;
+    a.pairs = d_pairs;
+    a.res = d_res;
+    a.queue = (int32_t *)c->queue.p;
+    const int wave = std::min<int>(c->n_timed, kMaxTimed - 1);   // past the cap the last slot is reused
+    while ((int)c->wave_t0.size() <= wave) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ABEA_ERR_CUDA;
+        c->wave_t0.push_back(e0);
+        c->wave_t1.push_back(e1);
+    }
+    if ((rc = cuda_err(cudaEventRecord(c->wave_t0[wave], st)))) return rc;
+    const int launch_grid = std::min<int>(grid, std::max<int>(1, (n + 3) / 4));
+    if ((rc = cuda_err((cudaError_t)abea::launch_align(a, g.C, g.mixed, launch_grid, st)))) return rc;
+    c->last_launches++;
+    if ((rc = cuda_err(cudaEventRecord(c->wave_t1[wave], st)))) return rc;
+    if (c->n_timed < kMaxTimed) c->n_timed++;
+    return ABEA_OK;
+}
+
+int check_common(abea_ctx *c, int W)
+{
+    if (!c) return ABEA_ERR_ARG;
+    if (c->k <= 0) return ABEA_ERR_NO_MODEL;
+    if (W < 2 || W > 256) return ABEA_ERR_ARG;
+    return ABEA_OK;
+}
+
+// Make `st` wait for the previous batch of this context (buffers are reused).
+int order_after_previous(abea_ctx *c, cudaStream_t st)
+{
+    return cuda_err(cudaStreamWaitEvent(st, c->batch_done, 0));
+}
+
+bool is_page_locked(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// One wave whose host buffers are all page-locked: copy straight from and
+// to the caller's arrays (no staging copy on the host).
+int packed_direct(abea_ctx *c, const Geometry &g, int32_t n, int W, const char *seq, const int64_t *seq_off,
+                  const float *events, const int64_t *ev_off, const abea_scalings *sc, abea_result *out,
+                  int32_t *pairs, const int64_t *pair_off, cudaStream_t st)
+{
+    int rc;
+    const int64_t ns = seq_off[n] - seq_off[0], ne = ev_off[n] - ev_off[0], np = pair_off[n] - pair_off[0];
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    if ((rc = ensure_host(c->h_rd, (size_t)n * sizeof(ReadDesc)))) return rc;
+    if ((rc = ensure_host(c->h_order, (size_t)n * sizeof(int32_t)))) return rc;
+    std::vector<int32_t> ids(n);
+    std::iota(ids.begin(), ids.end(), 0);
+    std::vector<int64_t> sb(n), eb(n), pb(n);
+    std::vector<int32_t> pc(n);
+    for (int32_t i = 0; i < n; i++) {
+        sb[i] = seq_off[i] - seq_off[0];
+        eb[i] = ev_off[i] - ev_off[0];
+        pb[i] = pair_off[i] - pair_off[0];
+        pc[i] = (int32_t)(pair_off[i + 1] - pair_off[i]);
+    }
+    Footprint f;
+    plan_reads(c, g, ids, seq_off, ev_off, sc, sb, eb, pb, pc, (ReadDesc *)c->h_rd.p, (int32_t *)c->h_order.p, f);
+    if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1)))) return rc;
+    if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4))) return rc;
+    if ((rc = ensure_dev(c, c->res, (size_t)n * sizeof(abea_result)))) return rc;
+    if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->seq.p, seq + seq_off[0], (size_t)ns, cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->events.p, events + ev_off[0], 4 * (size_t)ne, cudaMemcpyHostToDevice, st))))
+        return rc;
+    rc = run_wave(c, g, n, f, (const ReadDesc *)c->h_rd.p, (const int32_t *)c->h_order.p, (const uint8_t *)c->seq.p,
+                  (const float *)c->events.p, (abea_result *)c->res.p, (int32_t *)c->pairs.p, W, st);
+    if (rc) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(out, c->res.p, (size_t)n * sizeof(abea_result), cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if (np > 0 && (rc = cuda_err(cudaMemcpyAsync(pairs + 2 * pair_off[0], c->pairs.p, 8 * (size_t)np,
+                                                 cudaMemcpyDeviceToHost, st))))
+        return rc;
+    if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *abea_strerror(int code)
+{
+    switch (code) {
+    case ABEA_OK: return "ok";
+    case ABEA_ERR_ARG: return "invalid argument";
+    case ABEA_ERR_CAPACITY: return "output capacity too small";
+    case ABEA_ERR_NOMEM: return "out of memory or memory budget too small";
+    case ABEA_ERR_CUDA: return "CUDA runtime error";
+    case ABEA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case ABEA_ERR_NO_MODEL: return "no pore model set";
+    default: return "unknown error";
+    }
+}
+
+int abea_create(abea_ctx **out, int device, size_t mem_budget_bytes)
+{
+    if (!out) return ABEA_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return ABEA_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return ABEA_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    abea_ctx *c = new (std::nothrow) abea_ctx();
+    if (!c) return ABEA_ERR_NOMEM;
+    c->device = device;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->batch_done, cudaEventDisableTiming) != cudaSuccess) {
+        abea_destroy(c);
+        return cuda_err(cudaErrorUnknown);
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        abea_destroy(c);
+        return cuda_err(cudaErrorUnknown);
+    }
+    c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)free_b);
+    cudaEventRecord(c->batch_done, c->own_stream);
+    *out = c;
+    return ABEA_OK;
+}
+
+void abea_destroy(abea_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    cudaDeviceSynchronize();
+    DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->lle,
+                     &c->queue, &c->events, &c->seq, &c->res, &c->pairs};
+    for (DevBuf *b : dev) free_dev(*b);
+    HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs};
+    for (HostBuf *b : host) free_host(*b);
+    for (cudaEvent_t e : c->wave_t0) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->wave_t1) cudaEventDestroy(e);
+    if (c->t0) cudaEventDestroy(c->t0);
+    if (c->t1) cudaEventDestroy(c->t1);
+    if (c->upload_done) cudaEventDestroy(c->upload_done);
+    if (c->batch_done) cudaEventDestroy(c->batch_done);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int abea_set_model(abea_ctx *c, int k, const float *level_mean, const float *level_stdv)
+{
+    if (!c || !level_mean || !level_stdv || k < 1 || k > 12) return ABEA_ERR_ARG;
+    const size_t rows = (size_t)1 << (2 * k);
+    std::vector<ModelRow> m(rows);
+    for (size_t r = 0; r < rows; r++) {
+        const float mu = level_mean[r], sd = level_stdv[r];
+        if (!std::isfinite(mu) || !std::isfinite(sd) || !(sd > 0.0f)) return ABEA_ERR_ARG;
+        m[r].mu = (double)mu;
+        m[r].a0 = kSqrtHalf / (double)sd;
+        m[r].c0 = kLogInvSqrt2Pi - std::log((double)sd);
+        m[r].pad = 0.0;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    if (cudaStreamSynchronize(c->own_stream) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return cuda_err(cudaErrorUnknown);
+    if (c->model.cap < rows * sizeof(ModelRow)) {
+        free_dev(c->model);
+        if (cudaMalloc(&c->model.p, rows * sizeof(ModelRow)) != cudaSuccess) {
+            cudaGetLastError();
+            return ABEA_ERR_NOMEM;
+        }
+        c->model.cap = rows * sizeof(ModelRow);
+    }
+    int rc = cuda_err(cudaMemcpy(c->model.p, m.data(), rows * sizeof(ModelRow), cudaMemcpyHostToDevice));
+    if (rc) return rc;
+    c->k = k;
+    return ABEA_OK;
+}
+
+int abea_align_batch_device(abea_ctx *c, int32_t n, int W, const uint8_t *d_seq, const int64_t *seq_off,
+                            const float *d_events, const int64_t *ev_off, const abea_scalings *sc,
+                            abea_result *d_out, int32_t *d_pairs, const int64_t *pair_off, void *cuda_stream)
+{
+    int rc = check_common(c, W);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!seq_off || !ev_off || !sc || !pair_off || !d_out))) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    if (!d_seq || !d_events || (!d_pairs && pair_off[n] > 0)) return ABEA_ERR_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (seq_off[i + 1] < seq_off[i] || ev_off[i + 1] < ev_off[i] || pair_off[i + 1] < pair_off[i] ||
+            pair_off[i + 1] - pair_off[i] > INT32_MAX)
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    const Geometry g = abea::geometry_for(W);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    if ((rc = order_after_previous(c, st))) return rc;
+    // the pinned descriptor staging may still feed the previous upload
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    if ((rc = ensure_host(c->h_rd, (size_t)n * sizeof(ReadDesc)))) return rc;
+    if ((rc = ensure_host(c->h_order, (size_t)n * sizeof(int32_t)))) return rc;
+    std::vector<int32_t> ids(n);
+    std::iota(ids.begin(), ids.end(), 0);
+    std::vector<int64_t> sb(seq_off, seq_off + n), eb(ev_off, ev_off + n), pb(pair_off, pair_off + n);
+    std::vector<int32_t> pc(n);
+    for (int32_t i = 0; i < n; i++) pc[i] = (int32_t)(pair_off[i + 1] - pair_off[i]);
+    Footprint f;
+    plan_reads(c, g, ids, seq_off, ev_off, sc, sb, eb, pb, pc, (ReadDesc *)c->h_rd.p, (int32_t *)c->h_order.p, f);
+    if (work_bytes((size_t)n, f) > c->budget) return ABEA_ERR_NOMEM;
+    rc = run_wave(c, g, n, f, (const ReadDesc *)c->h_rd.p, (const int32_t *)c->h_order.p, d_seq, d_events, d_out,
+                  d_pairs, W, st);
+    if (rc) return rc;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+int abea_align_packed(abea_ctx *c, int32_t n, int W, const char *seq, const int64_t *seq_off, const float *events,
+                      const int64_t *ev_off, const abea_scalings *sc, abea_result *out, int32_t *pairs,
+                      const int64_t *pair_off, void *cuda_stream)
+{
+    int rc = check_common(c, W);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!seq || !seq_off || !events || !ev_off || !sc || !out || !pair_off))) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    if (!pairs && pair_off[n] > pair_off[0]) return ABEA_ERR_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (seq_off[i + 1] < seq_off[i] || ev_off[i + 1] < ev_off[i] || pair_off[i + 1] < pair_off[i] ||
+            pair_off[i + 1] - pair_off[i] > INT32_MAX)
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    const Geometry g = abea::geometry_for(W);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    if ((rc = order_after_previous(c, st))) return rc;
+
+    // waves: reads in decreasing length, each wave within the memory budget
+    std::vector<int32_t> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    auto len = [&](int32_t i) { return (ev_off[i + 1] - ev_off[i]) + (seq_off[i + 1] - seq_off[i]); };
+    std::stable_sort(all.begin(), all.end(), [&](int32_t a, int32_t b) { return len(a) > len(b); });
+    std::vector<std::vector<int32_t>> waves;
+    {
+        std::vector<int32_t> cur;
+        size_t cur_bytes = 0;
+        for (int32_t i : all) {
+            const int64_t n_e = ev_off[i + 1] - ev_off[i];
+            const int64_t n_k = (seq_off[i + 1] - seq_off[i]) - c->k + 1;
+            const Footprint f = footprint(std::max<int64_t>(n_e, 0), std::max<int64_t>(n_k, 0), g);
+            const size_t io = (size_t)(seq_off[i + 1] - seq_off[i]) + 4 * (size_t)n_e +
+                              8 * (size_t)(pair_off[i + 1] - pair_off[i]) + sizeof(abea_result);
+            const size_t bytes = work_bytes(1, f) + io;
+            if (bytes > c->budget) return ABEA_ERR_NOMEM;
+            if (!cur.empty() && cur_bytes + bytes > c->budget) {
+                waves.push_back(cur);
+                cur.clear();
+                cur_bytes = 0;
+            }
+            cur.push_back(i);
+            cur_bytes += bytes;
+        }
+        if (!cur.empty()) waves.push_back(cur);
+    }
+    if (waves.size() == 1 && is_page_locked(seq) && is_page_locked(events) && is_page_locked(out) &&
+        (pair_off[n] == pair_off[0] || is_page_locked(pairs)))
+        return packed_direct(c, g, n, W, seq, seq_off, events, ev_off, sc, out, pairs, pair_off, st);
+    for (const std::vector<int32_t> &ids : waves) {
+        const int32_t m = (int32_t)ids.size();
+        // gather the wave's inputs into pinned staging
+        std::vector<int64_t> sb(m), eb(m), pb(m);
+        std::vector<int32_t> pc(m);
+        int64_t ns = 0, ne = 0, np = 0;
+        for (int32_t t = 0; t < m; t++) {
+            const int32_t i = ids[t];
+            sb[t] = ns;
+            eb[t] = ne;
+            pb[t] = np;
+            pc[t] = (int32_t)(pair_off[i + 1] - pair_off[i]);
+            ns += seq_off[i + 1] - seq_off[i];
+            ne += ev_off[i + 1] - ev_off[i];
+            np += pc[t];
+        }
+        if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+        if ((rc = ensure_host(c->h_seq, std::max<int64_t>(ns, 1)))) return rc;
+        if ((rc = ensure_host(c->h_events, std::max<int64_t>(ne, 1) * 4))) return rc;
+        if ((rc = ensure_host(c->h_rd, (size_t)m * sizeof(ReadDesc)))) return rc;
+        if ((rc = ensure_host(c->h_order, (size_t)m * sizeof(int32_t)))) return rc;
+        if ((rc = ensure_host(c->h_res, (size_t)m * sizeof(abea_result)))) return rc;
+        if ((rc = ensure_host(c->h_pairs, std::max<int64_t>(np, 1) * 8))) return rc;
+        for (int32_t t = 0; t < m; t++) {
+            const int32_t i = ids[t];
+            std::memcpy((char *)c->h_seq.p + sb[t], seq + seq_off[i], (size_t)(seq_off[i + 1] - seq_off[i]));
+            std::memcpy((float *)c->h_events.p + eb[t], events + ev_off[i], 4 * (size_t)(ev_off[i + 1] - ev_off[i]));
+        }
+        std::vector<int64_t> s_off(m + 1), e_off(m + 1);
+        std::vector<abea_scalings> wsc(m);
+        for (int32_t t = 0; t < m; t++) {
+            s_off[t] = sb[t];
+            e_off[t] = eb[t];
+            wsc[t] = sc[ids[t]];
+        }
+        s_off[m] = ns;
+        e_off[m] = ne;
+        std::vector<int32_t> loc(m);
+        std::iota(loc.begin(), loc.end(), 0);
+        Footprint f;
+        plan_reads(c, g, loc, s_off.data(), e_off.data(), wsc.data(), sb, eb, pb, pc, (ReadDesc *)c->h_rd.p,
+                   (int32_t *)c->h_order.p, f);
+        if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1)))) return rc;
+        if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4))) return rc;
+        if ((rc = ensure_dev(c, c->res, (size_t)m * sizeof(abea_result)))) return rc;
+        if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8))) return rc;
+        if ((rc = cuda_err(cudaMemcpyAsync(c->seq.p, c->h_seq.p, (size_t)ns, cudaMemcpyHostToDevice, st)))) return rc;
+        if ((rc = cuda_err(cudaMemcpyAsync(c->events.p, c->h_events.p, 4 * (size_t)ne, cudaMemcpyHostToDevice, st))))
+            return rc;
+        rc = run_wave(c, g, m, f, (const ReadDesc *)c->h_rd.p, (const int32_t *)c->h_order.p,
+                      (const uint8_t *)c->seq.p, (const float *)c->events.p, (abea_result *)c->res.p,
+                      (int32_t *)c->pairs.p, W, st);
+        if (rc) return rc;
+        if ((rc = cuda_err(cudaMemcpyAsync(c->h_res.p, c->res.p, (size_t)m * sizeof(abea_result),
+                                           cudaMemcpyDeviceToHost, st))))
+            return rc;
+        if (np > 0 && (rc = cuda_err(cudaMemcpyAsync(c->h_pairs.p, c->pairs.p, 8 * (size_t)np,
+                                                     cudaMemcpyDeviceToHost, st))))
+            return rc;
+        if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+        const abea_result *hr = (const abea_result *)c->h_res.p;
+        for (int32_t t = 0; t < m; t++) {
+            const int32_t i = ids[t];
+            out[i] = hr[t];
+            const int32_t cnt = std::min<int32_t>(hr[t].n_pairs, pc[t]);
+            if (hr[t].status == ABEA_READ_OK && cnt > 0)
+                std::memcpy(pairs + 2 * pair_off[i], (const int32_t *)c->h_pairs.p + 2 * pb[t], 8 * (size_t)cnt);
+        }
+    }
+    return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+int abea_align_batch(abea_ctx *c, const abea_read *reads, int32_t n, int W, abea_result *out, int32_t *pairs,
+                     const int64_t *pair_off, void *cuda_stream)
+{
+    if (!c || n < 0 || (n > 0 && (!reads || !out || !pair_off))) return ABEA_ERR_ARG;
+    std::vector<int64_t> so(n + 1, 0), eo(n + 1, 0);
+    for (int32_t i = 0; i < n; i++) {
+        if (reads[i].n_events < 0 || reads[i].seq_len < 0) return ABEA_ERR_ARG;
+        if ((reads[i].n_events > 0 && !reads[i].ev_mean) || (reads[i].seq_len > 0 && !reads[i].seq)) return ABEA_ERR_ARG;
+        so[i + 1] = so[i] + reads[i].seq_len;
+        eo[i + 1] = eo[i] + reads[i].n_events;
+    }
+    std::vector<char> s((size_t)std::max<int64_t>(so[n], 1));
+    std::vector<float> e((size_t)std::max<int64_t>(eo[n], 1));
+    std::vector<abea_scalings> sc(std::max<int32_t>(n, 1));
+    for (int32_t i = 0; i < n; i++) {
+        if (reads[i].seq_len) std::memcpy(s.data() + so[i], reads[i].seq, (size_t)reads[i].seq_len);
+        if (reads[i].n_events) std::memcpy(e.data() + eo[i], reads[i].ev_mean, 4 * (size_t)reads[i].n_events);
+        sc[i] = reads[i].sc;
+    }
+    return abea_align_packed(c, n, W, s.data(), so.data(), e.data(), eo.data(), sc.data(), out, pairs, pair_off,
+                             cuda_stream);
+}
+
+int abea_align(abea_ctx *c, const abea_read *read, int W, abea_result *out, int32_t *pairs, int32_t cap)
+{
+    if (!c || !read || !out || cap < 0 || (cap > 0 && !pairs)) return ABEA_ERR_ARG;
+    const int64_t po[2] = {0, cap};
+    int rc = abea_align_batch(c, read, 1, W, out, pairs, po, nullptr);
+    if (rc) return rc;
+    if (out->status == ABEA_READ_CAPACITY) return ABEA_ERR_CAPACITY;
+    return ABEA_OK;
+}
+
+int abea_last_launch_stats(abea_ctx *c, int32_t *n_launches, float *align_kernel_ms)
+{
+    if (!c) return ABEA_ERR_ARG;
+    float total = 0.0f;
+    int rc = ABEA_OK;
+    for (int w = 0; w < c->n_timed; w++) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(c->wave_t1[w]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->wave_t0[w], c->wave_t1[w]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = ABEA_ERR_CUDA;
+            break;
+        }
+        total += ms;
+    }
+    if (n_launches) *n_launches = c->last_launches;
+    if (align_kernel_ms) *align_kernel_ms = total;
+    c->n_timed = 0;
+    c->last_launches = 0;
+    return rc;
+}
+
+}  // extern "C"

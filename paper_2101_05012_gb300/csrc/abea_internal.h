@@ -1,0 +1,70 @@
+// Internal declarations shared by the host API and the kernels of libabea.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/abea.h"
+
+namespace abea {
+
+// Per-read descriptor, built on the host for every batch (thesis Sec. "Data
+// array serialisation": one flat array per kind of data plus per-read
+// offsets into each).
+struct ReadDesc {
+    int64_t ev_off;     // first event of the read in the events array
+    int64_t seq_off;    // first base of the read in the bases array
+    int64_t kc_off;     // first k-mer cache entry (float4 units)
+    int64_t tr_off;     // first trace word (uint32 units); one record of rec_words per band
+    int64_t ll_off;     // first per-band record of ll_e (int32)
+    int64_t pair_off;   // first output pair (int2 units)
+    int32_t n_e;        // events
+    int32_t n_k;        // k-mers
+    int32_t pair_cap;   // output pair capacity
+    int32_t host_bad;   // rejected on the host (counts, scalings)
+    float lp_skip, lp_stay, lp_step, lp_trim;   // transition constants, FP64 rounded once
+    double scale, shift, inv_var, log_var;      // read-model scaling, FP64
+};
+static_assert(sizeof(ReadDesc) == 112, "descriptor layout");
+
+// Per model row: mean, sqrt(1/2)/stdv and ln(1/sqrt(2 pi)) - ln(stdv), FP64.
+struct ModelRow {
+    double mu;
+    double a0;
+    double c0;
+    double pad;
+};
+
+// Band-record geometry for a band width W: C offsets per lane, L lanes,
+// W' = C*L >= W physical offsets, rec_words uint32 words of trace per band.
+struct Geometry {
+    int C, L, Wp, rec_words;
+    bool mixed;
+};
+Geometry geometry_for(int W);
+
+struct AlignArgs {
+    const ReadDesc *rd;
+    const int32_t *order;      // reads in processing order (longest first)
+    const int32_t *flags;      // nonzero: bad input found on the device
+    int32_t n;
+    int32_t W;
+    int32_t L;
+    const float *events;
+    const uint8_t *seq;
+    const float4 *kc;
+    uint32_t *trace;
+    int32_t *lle;              // per band: event index of the band's offset-0 cell
+    int32_t *pairs;            // int32 pairs, (event, k-mer)
+    abea_result *res;
+    int32_t *queue;            // work counter, zeroed before the launch
+};
+
+// Launchers (return cudaError_t as int).
+int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *events,
+                const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
+int launch_align(const AlignArgs &a, int C, bool mixed, int grid, void *stream);
+int align_grid_size(int C, bool mixed, int device);
+
+}  // namespace abea

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: per-read status, end event, in-matrix cell count and the pair list are
+identical to the FP32 oracle's; the FP32 score is bit-identical to the FP32
+oracle's (both take every decision on the same FP32 values) and within 1e-4
+relative of the FP64 oracle's.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2101_05012_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, batch, W=None, **kw):
+    ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
+    return ctx.align_packed(batch, W=W, **kw)
+
+
+def gpu_pairs(pairs, pair_off, res, i):
+    return pairs[pair_off[i]:pair_off[i] + res["n_pairs"][i]]
+
+
+def compare(batch, res, pairs, pair_off, W=None, check_f64=True, ids=None):
+    """Compare GPU results of `batch` with the oracle (all reads, or `ids`)."""
+    W = batch.W if W is None else W
+    sub = batch if ids is None else batch.subset(ids)
+    idx = np.arange(batch.n) if ids is None else np.asarray(ids)
+    o32 = oracle.abea_batch(sub, "f32", n_threads=THREADS, W=W)
+    o64 = oracle.abea_batch(sub, "f64", n_threads=THREADS, W=W) if check_f64 else None
+    bad = []
+    for t, i in enumerate(idx):
+        st = int(res["status"][i])
+        if st != int(o32["status"][t]):
+            bad.append((i, "status", st, int(o32["status"][t])))
+            continue
+        if st != oracle.ST_OK:
+            continue
+        if np.float32(o32["score"][t]) != res["score"][i]:
+            bad.append((i, "score", float(res["score"][i]), o32["score"][t]))
+        if int(res["e_end"][i]) != int(o32["e_end"][t]) or int(res["cells"][i]) != int(o32["cells"][t]):
+            bad.append((i, "e_end/cells", int(res["e_end"][i]), int(o32["e_end"][t]), int(res["cells"][i]),
+                        int(o32["cells"][t])))
+        a = gpu_pairs(pairs, pair_off, res, i)
+        b = o32["pairs"][o32["pair_off"][t]:o32["pair_off"][t] + o32["n_pairs"][t]]
+        if not np.array_equal(a, b):
+            bad.append((i, "pairs", len(a), len(b)))
+        if o64 is not None and o64["status"][t] == oracle.ST_OK:
+            rel = abs(float(res["score"][i]) - o64["score"][t]) / abs(o64["score"][t])
+            if rel > 1e-4:
+                bad.append((i, "f64", rel))
+    assert not bad, bad[:10]
+    return o32, o64
+
+
+def test_plain_64x1kb(ctx):
+    b = synth.make_batch("plain_64x1kb")
+    res, pairs, po = run_gpu(ctx, b)
+    assert np.all(res["status"] == 0)
+    compare(b, res, pairs, po)
+
+
+def _lengths_batch(lengths, k=6, W=100, seed=5, dwell_mean=1.8):
+    w = synth.Workload("ragged", len(lengths), k, W, seed, ("fixed", 1), dwell_mean=dwell_mean)
+    mm, ms = synth.make_model(k, seed)
+    reads = [synth.make_read(w, r, max(L, 1), mm, ms) for r, L in enumerate(lengths)]
+    seqs = [r[0][:L].tobytes() for r, L in zip(reads, lengths)]
+    return synth.custom_batch([r[1] for r in reads], seqs, [r[2] for r in reads], mm, ms, k, W)
+
+
+def test_ragged_lengths(ctx):
+    lengths = [6, 7, 8, 10, 20, 49, 50, 51, 52, 99, 100, 101, 102, 103, 150, 151, 300, 999, 1000, 2500, 3001]
+    b = _lengths_batch(lengths)
+    res, pairs, po = run_gpu(ctx, b)
+    compare(b, res, pairs, po)
+
+
+@pytest.mark.parametrize("W", [2, 3, 4, 5, 7, 16, 31, 32, 33, 50, 63, 64, 65, 100, 101, 127, 128, 129, 160, 200,
+                               201, 255, 256])
+def test_band_widths(ctx, W):
+    lengths = [6, 9, 30, 80, 150, 260, 420, 700]
+    b = _lengths_batch(lengths, W=W, seed=W)
+    res, pairs, po = run_gpu(ctx, b, W=W)
+    compare(b, res, pairs, po, W=W)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 7, 9])
+def test_kmer_sizes(ctx, k):
+    lengths = [k, k + 1, 40, 300, 900]
+    b = _lengths_batch(lengths, k=k, seed=10 + k)
+    res, pairs, po = run_gpu(ctx, b)
+    compare(b, res, pairs, po)
+
+
+def test_bad_inputs_and_neighbours(ctx):
+    good = _lengths_batch([300, 500, 700], seed=3)
+    ev, sq, sc = [], [], []
+    for i in range(good.n):
+        e, s, c = good.read(i)
+        ev.append(e)
+        sq.append(s)
+        sc.append(c)
+    e0, s0, c0 = ev[0], sq[0], sc[0]
+    bad_seq = s0[:50] + b"N" + s0[51:]
+    nan_ev = e0.copy()
+    nan_ev[7] = np.nan
+    inf_ev = e0.copy()
+    inf_ev[-1] = np.inf
+    cases = [(e0, bad_seq, c0), (nan_ev, s0, c0), (inf_ev, s0, c0), (e0, s0, (1.0, 0.0, 0.0)),
+             (e0[:0], s0, c0), (e0, s0[:5], c0), (e0, s0, (np.nan, 0.0, 1.0))]
+    all_ev = [ev[1]] + [c[0] for c in cases] + [ev[2]]
+    all_sq = [sq[1]] + [c[1] for c in cases] + [sq[2]]
+    all_sc = [sc[1]] + [c[2] for c in cases] + [sc[2]]
+    b = synth.custom_batch(all_ev, all_sq, all_sc, good.model_mean, good.model_stdv, good.k, good.W)
+    res, pairs, po = run_gpu(ctx, b)
+    assert res["status"][0] == 0 and res["status"][-1] == 0
+    assert np.all(res["status"][1:-1] == binding.READ_BAD_INPUT), res["status"]
+    assert np.all(np.isneginf(res["score"][1:-1]))
+    compare(b, res, pairs, po, ids=[0, b.n - 1])
+
+
+def test_capacity(ctx):
+    b = _lengths_batch([200, 400, 600], seed=8)
+    o = oracle.abea_batch(b, "f32", n_threads=THREADS)
+    need = o["n_pairs"]
+    caps = need.astype(np.int64).copy()
+    caps[1] = need[1] - 1                        # one pair short
+    po = np.zeros(b.n + 1, np.int64)
+    np.cumsum(caps, out=po[1:])
+    res, pairs, po = run_gpu(ctx, b, pair_off=po)
+    assert res["status"][1] == binding.READ_CAPACITY and res["n_pairs"][1] == need[1]
+    assert res["status"][0] == 0 and res["status"][2] == 0
+    for i in (0, 2):
+        assert np.array_equal(gpu_pairs(pairs, po, res, i), o["pairs"][o["pair_off"][i]:o["pair_off"][i] + need[i]])
+    # the single-read call reports the shortfall as ABEA_ERR_CAPACITY
+    ctx.set_model(b.k, b.model_mean, b.model_stdv)
+    e, s, c = b.read(1)
+    import ctypes
+    ev = np.ascontiguousarray(e, np.float32)
+    sq = np.frombuffer(s, np.uint8).copy()
+    rd = binding.Read(binding._p(ev).value, len(ev), binding._p(sq).value, len(sq), binding.Scalings(*c))
+    out = binding.Result()
+    buf = np.zeros((need[1], 2), np.int32)
+    rc = ctx.lib.abea_align(ctx.h, ctypes.byref(rd), b.W, ctypes.byref(out), binding._p(buf), int(need[1]) - 1)
+    assert rc == binding.ABEA_ERR_CAPACITY and out.n_pairs == need[1]
+
+
+def test_extreme_events(ctx):
+    # events far outside the model: the FP32 emission overflows to -inf
+    # (z^2 > 3.4e38), leaving only trim/skip paths for those cells
+    rng = np.random.default_rng(4)
+    base = _lengths_batch([40, 60, 90, 200, 400], seed=44)
+    evs, sqs, scs = [], [], []
+    for i in range(base.n):
+        e, s, c = base.read(i)
+        e = e.copy()
+        pos = rng.choice(len(e), max(1, len(e) // 10), replace=False)
+        e[pos] = rng.choice(np.array([1e20, -1e20, 3e4, -3e4], np.float32), len(pos))
+        evs.append(e)
+        sqs.append(s)
+        scs.append(c)
+    b = synth.custom_batch(evs, sqs, scs, base.model_mean, base.model_stdv, base.k, base.W)
+    for W in (3, 100):
+        res, pairs, po = run_gpu(ctx, b, W=W)
+        compare(b, res, pairs, po, W=W, check_f64=False)
+
+
+def test_single_read_call_matches_batch(ctx):
+    b = synth.make_batch("plain_64x1kb", n_reads=3)
+    res, pairs, po = run_gpu(ctx, b)
+    for i in range(b.n):
+        e, s, c = b.read(i)
+        r1, p1 = ctx.align(e, s, c, b.W)
+        assert r1["status"] == 0 and np.float32(r1["score"]) == res["score"][i]
+        assert np.array_equal(p1, gpu_pairs(pairs, po, res, i))
+
+
+def test_align_batch_records(ctx):
+    b = synth.make_batch("plain_64x1kb", n_reads=5)
+    res, pairs, po = run_gpu(ctx, b)
+    evs, sqs, scs = zip(*[b.read(i) for i in range(b.n)])
+    r2, p2, po2 = ctx.align_batch(list(evs), list(sqs), list(scs), b.W)
+    assert np.array_equal(res, r2)
+    for i in range(b.n):
+        assert np.array_equal(gpu_pairs(pairs, po, res, i), gpu_pairs(p2, po2, r2, i))
+
+
+def test_device_api_matches_host_api(ctx):
+    torch = pytest.importorskip("torch")
+    b = synth.make_batch("plain_64x1kb", n_reads=20)
+    res, pairs, po = run_gpu(ctx, b)
+    dev = torch.device("cuda", 0)
+    d_seq = torch.from_numpy(b.seq).to(dev)
+    d_ev = torch.from_numpy(b.events).to(dev)
+    d_out = torch.zeros(b.n * 24, dtype=torch.uint8, device=dev)
+    d_pairs = torch.zeros(int(po[-1]) * 2, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    s = torch.cuda.Stream(dev)            # a real stream: NULL would select the context's own stream
+    ctx.align_batch_device(b.n, b.W, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_out, d_pairs, po,
+                           stream=s.cuda_stream)
+    s.synchronize()
+    r2 = binding.results_from_bytes(d_out.cpu().numpy())
+    p2 = d_pairs.cpu().numpy().reshape(-1, 2)
+    assert np.array_equal(res, r2)
+    for i in range(b.n):
+        assert np.array_equal(gpu_pairs(pairs, po, res, i), gpu_pairs(p2, po, r2, i))
+
+
+def test_memory_budget_waves():
+    b = synth.make_batch("plain_64x1kb", n_reads=24)
+    with binding.Context(0) as big:
+        r1, p1, po1 = run_gpu(big, b)
+    # a budget of roughly three reads' working set (~130 KB each) forces many waves
+    with binding.Context(0, mem_budget_bytes=400_000) as small:
+        r2, p2, po2 = run_gpu(small, b)
+        launches, _ = small.last_launch_stats()
+    assert launches >= 2 * 6            # a pre-kernel and a core kernel per wave
+    assert np.array_equal(r1, r2)
+    assert np.array_equal(p1, p2)
+
+
+def test_batch_4096_ln5kb_full(ctx):
+    """The one-launch batch workload at full size: every read against the FP32
+    oracle (FP64 on a sample)."""
+    b = synth.make_batch("batch_4096_ln5kb")
+    res, pairs, po = run_gpu(ctx, b)
+    assert np.all(res["status"] == 0)
+    compare(b, res, pairs, po, check_f64=False)
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.choice(b.n, 48, replace=False).tolist()) | {int(np.argmax(b.n_events()))})
+    compare(b, res, pairs, po, ids=sample)
+
+
+def test_wide_k9_w200_sample(ctx):
+    w = synth.WORKLOADS["wide_10k_ln10kb_k9_w200"]
+    b = synth.make_batch(w, read_ids=range(0, w.n_reads, w.n_reads // 40))
+    res, pairs, po = run_gpu(ctx, b)
+    assert np.all(res["status"] == 0)
+    compare(b, res, pairs, po)

@@ -41,8 +41,11 @@ MUTANTS = [
     ("diag_from_previous_band", "? SCORE(b - 2, j_diag)", "? SCORE(b - 1, j_diag)"),
     ("sk_rule_reversed", "advance_kmer = lower_left < upper_right;", "advance_kmer = lower_left > upper_right;"),
     ("trim_count", "SCORE(b, jt) = (real)(e + 1) * p.lp_trim;", "SCORE(b, jt) = (real)(e) * p.lp_trim;"),
-    ("end_trim_count", "real cand = SCORE(b, j) + (real)(n_e - 1 - e) * p.lp_trim;",
-     "real cand = SCORE(b, j) + (real)(n_e - e) * p.lp_trim;"),
+    ("end_trim_count", "band_frame[b] + (double)(SCORE(b, j) + (real)(n_e - 1 - e) * p.lp_trim);",
+     "band_frame[b] + (double)(SCORE(b, j) + (real)(n_e - e) * p.lp_trim);"),
+    ("f32_frame_not_added_back", "double cand = band_frame[b] + (double)(SCORE(b, j)",
+     "double cand = 0.0 + (double)(SCORE(b, j)"),
+    ("f32_renorm_shifts_one_band", "                    SCORE(b - 1, j) -= R;\n", ""),
     ("origin_offset", "ll_e[0] = half - 1;", "ll_e[0] = half;"),
     ("backtrack_up_moves_kmer", "else if (t == TR_U) { e--; }\n            else { kk--; }\n        }\n        if (overflow == 2)",
      "else if (t == TR_U) { kk--; }\n            else { kk--; }\n        }\n        if (overflow == 2)"),
@@ -64,7 +67,8 @@ CHILD = textwrap.dedent("""
             ("hand_f32", lambda: P.pin_hand_examples(lib, "f32")),
             ("brute_force", lambda: P.pin_brute_force(lib, n_cases=40)),
             ("wide_band", lambda: P.pin_wide_band_is_full_dp(lib, n_reads=3)),
-            ("invariants", lambda: P.pin_invariants(lib, n_reads=2))]
+            ("invariants", lambda: P.pin_invariants(lib, n_reads=2)),
+            ("fp32_long_read", lambda: P.pin_fp32_long_read(lib))]
     failed = []
     for name, fn in pins:
         try:

@@ -313,6 +313,27 @@ def test_fp32_vs_fp64(olib):
 
 
 # ----------------------------------------------------------------------------
+# FP32 on long reads (where the exact renormalisation of the FP32 form acts)
+# against FP64: same path unless near-tie, score within 2e-5 relative.
+
+def pin_fp32_long_read(lib):
+    w = synth.Workload("long", 2, 6, 100, 31, ("fixed", 20_000))
+    b = synth.make_batch(w)
+    for i in range(b.n):
+        ev, sq, sc = b.read(i)
+        r64 = oracle.abea(b.model_mean, b.model_stdv, b.k, sq, ev, sc, b.W, "f64", lib=lib)
+        r32 = oracle.abea(b.model_mean, b.model_stdv, b.k, sq, ev, sc, b.W, "f32", lib=lib)
+        assert r64["status"] == r32["status"] == oracle.ST_OK
+        assert abs(r32["score"] - r64["score"]) <= 2e-5 * abs(r64["score"]), (r32["score"], r64["score"])
+        if r64["min_margin"] >= 1e-3:
+            assert np.array_equal(r32["pairs"], r64["pairs"])
+
+
+def test_fp32_long_read(olib):
+    pin_fp32_long_read(olib)
+
+
+# ----------------------------------------------------------------------------
 # degenerate inputs
 
 def test_degenerate(olib):
