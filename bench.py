@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--reads", type=int, default=None, help="only the first N reads of the workload (profiling)")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -176,7 +177,7 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    batch = synth.make_batch(args.workload)
+    batch = synth.make_batch(args.workload, n_reads=args.reads)
     n = batch.n
     ctx = binding.Context(local_rank)
     ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)

@@ -52,14 +52,14 @@ struct abea_ctx {
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
     DevBuf model;
-    DevBuf rd, order, flags, kc, trace, lle, queue;
+    DevBuf rd, order, flags, kc, trace, moves, queue;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
     HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
     int32_t last_launches = 0;                  // kernel launches since the last stats call
-    int grid[9][2] = {};
+    int grid[9][2][2] = {};
 };
 
 namespace {
@@ -126,9 +126,9 @@ void free_host(HostBuf &b)
 
 cudaStream_t pick_stream(abea_ctx *c, void *s) { return s ? (cudaStream_t)s : c->own_stream; }
 
-// Per-read footprint in device memory (k-mer cache entries, trace words, ll_e records).
+// Per-read footprint in device memory (k-mer cache entries, trace words, move bytes).
 struct Footprint {
-    size_t kc, trace, lle;
+    size_t kc, trace, moves;
 };
 
 Footprint footprint(int64_t n_e, int64_t n_k, const Geometry &g)
@@ -137,7 +137,7 @@ Footprint footprint(int64_t n_e, int64_t n_k, const Geometry &g)
     Footprint f;
     f.kc = (size_t)std::max<int64_t>(n_k, 0);
     f.trace = (size_t)(bands * g.rec_words);
-    f.lle = (size_t)((bands + 3) / 4 * 4);
+    f.moves = g.full ? (size_t)((bands + 15) / 16 * 16) : 0;
     return f;
 }
 
@@ -187,10 +187,10 @@ int plan_reads(const abea_ctx *c, const Geometry &g, const std::vector<int32_t> 
             const Footprint f = footprint(n_e, n_k, g);
             d.kc_off = (int64_t)total.kc;
             d.tr_off = (int64_t)total.trace;
-            d.ll_off = (int64_t)total.lle;
+            d.mv_off = (int64_t)total.moves;
             total.kc += f.kc;
             total.trace += f.trace;
-            total.lle += f.lle;
+            total.moves += f.moves;
         }
         rd[t] = d;
     }
@@ -207,7 +207,7 @@ int plan_reads(const abea_ctx *c, const Geometry &g, const std::vector<int32_t> 
 // Device bytes one wave of `n` reads holds besides its inputs/outputs.
 size_t work_bytes(size_t n, const Footprint &f)
 {
-    return n * (sizeof(ReadDesc) + 2 * sizeof(int32_t)) + f.kc * 16 + f.trace * 4 + f.lle * 4 + 256;
+    return n * (sizeof(ReadDesc) + 2 * sizeof(int32_t)) + f.kc * 16 + f.trace * 4 + f.moves + 256;
 }
 
 // Enqueue prep + align for one planned wave whose descriptors/order are in
@@ -222,7 +222,7 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
     if ((rc = ensure_dev(c, c->flags, (size_t)n * sizeof(int32_t)))) return rc;
     if ((rc = ensure_dev(c, c->kc, std::max<size_t>(f.kc, 1) * 16))) return rc;
     if ((rc = ensure_dev(c, c->trace, std::max<size_t>(f.trace, 4) * 4))) return rc;
-    if ((rc = ensure_dev(c, c->lle, std::max<size_t>(f.lle, 4) * 4))) return rc;
+    if ((rc = ensure_dev(c, c->moves, std::max<size_t>(f.moves, 16)))) return rc;
     if ((rc = ensure_dev(c, c->queue, 256))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->rd.p, h_rd, (size_t)n * sizeof(ReadDesc), cudaMemcpyHostToDevice, st))))
         return rc;
@@ -235,8 +235,8 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
                                                        (int32_t *)c->flags.p, st))))
         return rc;
     c->last_launches++;
-    int &grid = c->grid[g.C][g.mixed ? 1 : 0];
-    if (grid <= 0) grid = abea::align_grid_size(g.C, g.mixed, c->device);
+    int &grid = c->grid[g.C][g.mixed ? 1 : 0][g.full ? 1 : 0];
+    if (grid <= 0) grid = abea::align_grid_size(g, c->device);
     if (grid <= 0) return ABEA_ERR_CUDA;
     AlignArgs a;
     a.rd = (const ReadDesc *)c->rd.p;
@@ -249,7 +249,7 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
     a.seq = d_seq;
     a.kc = (const float4 *)c->kc.p;
     a.trace = (uint32_t *)c->trace.p;
-    a.lle = (int32_t *)c->lle.p;
+    a.moves = (uint8_t *)c->moves.p;
     a.pairs = d_pairs;
     a.res = d_res;
     a.queue = (int32_t *)c->queue.p;
@@ -262,7 +262,7 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
     }
     if ((rc = cuda_err(cudaEventRecord(c->wave_t0[wave], st)))) return rc;
     const int launch_grid = std::min<int>(grid, std::max<int>(1, (n + 3) / 4));
-    if ((rc = cuda_err((cudaError_t)abea::launch_align(a, g.C, g.mixed, launch_grid, st)))) return rc;
+    if ((rc = cuda_err((cudaError_t)abea::launch_align(a, g, launch_grid, st)))) return rc;
     c->last_launches++;
     if ((rc = cuda_err(cudaEventRecord(c->wave_t1[wave], st)))) return rc;
     if (c->n_timed < kMaxTimed) c->n_timed++;
@@ -391,7 +391,7 @@ void abea_destroy(abea_ctx *c)
     cudaSetDevice(c->device);
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     cudaDeviceSynchronize();
-    DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->lle,
+    DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
                      &c->queue, &c->events, &c->seq, &c->res, &c->pairs};
     for (DevBuf *b : dev) free_dev(*b);
     HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs};

@@ -17,7 +17,7 @@ struct ReadDesc {
     int64_t seq_off;    // first base of the read in the bases array
     int64_t kc_off;     // first k-mer cache entry (float4 units)
     int64_t tr_off;     // first trace word (uint32 units); one record of rec_words per band
-    int64_t ll_off;     // first per-band record of ll_e (int32)
+    int64_t mv_off;     // first per-band move byte (used only when all 32 lanes hold the band)
     int64_t pair_off;   // first output pair (int2 units)
     int32_t n_e;        // events
     int32_t n_k;        // k-mers
@@ -37,10 +37,11 @@ struct ModelRow {
 };
 
 // Band-record geometry for a band width W: C offsets per lane, L lanes,
-// W' = C*L >= W physical offsets, rec_words uint32 words of trace per band.
+// W' = C*L >= W physical offsets (mixed: W' > W), full: L == 32 (no lane
+// above the band), rec_words uint32 words of trace per band.
 struct Geometry {
     int C, L, Wp, rec_words;
-    bool mixed;
+    bool mixed, full;
 };
 Geometry geometry_for(int W);
 
@@ -55,7 +56,7 @@ struct AlignArgs {
     const uint8_t *seq;
     const float4 *kc;
     uint32_t *trace;
-    int32_t *lle;              // per band: event index of the band's offset-0 cell
+    uint8_t *moves;            // per band: 1 if it moved by one k-mer (only when full)
     int32_t *pairs;            // int32 pairs, (event, k-mer)
     abea_result *res;
     int32_t *queue;            // work counter, zeroed before the launch
@@ -64,7 +65,7 @@ struct AlignArgs {
 // Launchers (return cudaError_t as int).
 int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *events,
                 const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
-int launch_align(const AlignArgs &a, int C, bool mixed, int grid, void *stream);
-int align_grid_size(int C, bool mixed, int device);
+int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream);
+int align_grid_size(const Geometry &g, int device);
 
 }  // namespace abea
