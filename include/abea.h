@@ -148,6 +148,33 @@ int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
  * between two calls (later ones are folded into the last slot). */
 int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
 
+/* The paper has no counterpart to this call.  abea_align_batch_device without
+ * any memory allocation, for callers that cannot call cudaMalloc: for
+ * example a plugin inside a host application that already holds (nearly)
+ * all device memory in its own pool, or a latency-critical path on which
+ * cudaMalloc/cudaFree, which may synchronise the device, are not allowed.
+ * No context is needed: the pore model (k <= 7, 4^k host floats each) is
+ * passed with every call, and all working memory (model rows, per-read
+ * descriptors, k-mer cache, trace) comes from one 64 MiB device array
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  Inputs, outputs, offsets and scalings are as in
+ * abea_align_batch_device; the work runs on the current device, on
+ * cuda_stream, and the call returns without waiting for it.
+ * Returns ABEA_ERR_NOMEM, before issuing any work, when n > 16384 or the
+ * batch's working set exceeds the 64 MiB array (at W = 100 about 0.33 B per
+ * band cell plus 16 B per k-mer and 120 B per read).
+ * Every call reuses the same array: calls whose work overlaps on the GPU
+ * (different streams or host threads) race and must not be made; issue them
+ * one after another on one stream, from one host thread at a time.  The first
+ * call on a device looks up the array's device address, so make it before
+ * any stream capture. */
+int abea_align_batch_device_noalloc(int k, const float *level_mean, const float *level_stdv,
+                                    int32_t n, int W,
+                                    const uint8_t *d_seq, const int64_t *seq_off,
+                                    const float *d_events, const int64_t *ev_off, const abea_scalings *sc,
+                                    abea_result *d_out, int32_t *d_pairs, const int64_t *pair_off,
+                                    void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

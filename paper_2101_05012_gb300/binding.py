@@ -27,7 +27,8 @@ READ_OK, READ_FAIL_NO_END, READ_BAD_INPUT, READ_CAPACITY = range(4)
 
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
-           "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats"]
+           "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
+           "abea_align_batch_device_noalloc"]
 
 
 class Scalings(ctypes.Structure):
@@ -81,6 +82,7 @@ def load(path: Optional[str] = None):
     lib.abea_align_packed.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_align_batch_device.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.abea_align_batch_device_noalloc.argtypes = [ctypes.c_int, P, P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     for f in EXPORTS:
         if f not in ("abea_destroy", "abea_strerror"):
             getattr(lib, f).restype = ctypes.c_int
@@ -201,6 +203,23 @@ class Context:
         ms = ctypes.c_float()
         _check(self.lib.abea_last_launch_stats(self.h, ctypes.byref(n), ctypes.byref(ms)), "abea_last_launch_stats")
         return n.value, ms.value
+
+
+def align_batch_device_noalloc(k: int, level_mean, level_stdv, n: int, W: int, d_seq, seq_off, d_events, ev_off,
+                               scalings, d_out, d_pairs, pair_off, stream=None):
+    """abea_align_batch_device_noalloc (no context, no allocation): d_* are torch CUDA
+    tensors on the current device; model, offsets and scalings are host arrays."""
+    lib = load()
+    mm = np.ascontiguousarray(level_mean, np.float32)
+    ms = np.ascontiguousarray(level_stdv, np.float32)
+    sc = np.ascontiguousarray(scalings, np.float32)
+    so = np.ascontiguousarray(seq_off, np.int64)
+    eo = np.ascontiguousarray(ev_off, np.int64)
+    po = np.ascontiguousarray(pair_off, np.int64)
+    _check(lib.abea_align_batch_device_noalloc(
+        k, _p(mm), _p(ms), n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()),
+        _p(eo), _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
+        ctypes.c_void_p(stream)), "abea_align_batch_device_noalloc")
 
 
 def results_from_bytes(buf: np.ndarray) -> np.ndarray:
