@@ -609,82 +609,70 @@ __device__ __forceinline__ unsigned chunk_event_moves(const ReadCtx &r, int top,
 }
 
 // Walk the trace from (e_end, n_k-1) (whose band has offset-0 event le_end)
-// until an index leaves the matrix, writing pair t of the walk to
+// until an index leaves the matrix; lane 0 writes pair t of the walk to
 // out[cap-1-t] (t < cap).  Returns 0, or -1 if a traced cell lies outside
-// its band (cannot happen); n_out = pairs walked.
+// its band (cannot happen); n_out = pairs walked.  The records of 96 bands
+// sit in a shared-memory ring of three 32-band chunks, the next two always
+// on their way (cp.async); the band moves of the current and next chunk are
+// kept as one 64-bit word, so a step needs one shared-memory load.
 template <int C, bool FULLW>
 __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end, int2 *out, int cap, int &n_out)
 {
     constexpr int R = Rec<C>::R;
-    const int lane = r.lane;
+    constexpr int RING = 3 * kChunk;
     int e = e_end, k = r.n_k - 1;
-    int bb = e + k + 2;
-    int le = le_end;
-    int top = bb;
-    int cur = 0;
+    int top = e + k + 2;               // band held in ring slot `base`
+    int base = 0;
     chunk_copy<C>(r, top, bufs);
     chunk_copy<C>(r, top - kChunk, bufs + kChunk * R);
     chunk_copy<C>(r, top - 2 * kChunk, bufs + 2 * kChunk * R);
     cp_async_wait<1>();
     __syncwarp();
-    unsigned em_cur = chunk_event_moves<C, FULLW>(r, top, bufs);
-    unsigned em_nxt = chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + kChunk * R);
+    // bit i: band top-i moved by one event
+    unsigned long long em = (unsigned long long)chunk_event_moves<C, FULLW>(r, top, bufs) |
+                            ((unsigned long long)chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + kChunk * R)
+                             << 32);
+    const bool writer = r.lane == 0;
+    int le = le_end;
+    int off = 0;                       // the current cell's band is top - off
     int n = 0;
-    int2 mine = make_int2(0, 0);
-    int status = 0;
-    while (e >= 0 && k >= 0) {
-        if (bb <= top - kChunk) {
-            // the next chunk becomes current; the copy issued one chunk ago is
-            // waited for; the freed buffer starts the copy two chunks ahead
+    unsigned bad = 0;
+    while (((e | k) >= 0) && !bad) {
+        const int j = le - e;
+        bad = (unsigned)j >= (unsigned)r.W ? 1u : 0u;
+        int p = base + off;
+        p -= (p >= RING) ? RING : 0;
+        const uint2 w = *reinterpret_cast<const uint2 *>(bufs + p * R + 2 * ((unsigned)j % C));
+        const unsigned bit = (unsigned)j / C;
+        if (writer && n < cap) out[cap - 1 - n] = make_int2(e, k);
+        n++;
+        const unsigned l = (w.y >> bit) & 1u;
+        const unsigned d = ((w.x >> bit) & 1u | l) ^ 1u;          // D: neither L nor U
+        const unsigned ev = (unsigned)(em >> off);                 // bit 0: band bb, bit 1: band bb-1
+        le -= (int)((ev & 1u) + ((ev >> 1) & d));
+        e -= (int)(l ^ 1u);                                        // U or D
+        k -= (int)(l | d);                                         // L or D
+        off += 1 + (int)d;
+        if (off >= kChunk) {           // the walk enters the next chunk
             __syncwarp();
-            const int freed = cur;
-            cur = (cur + 1) % 3;
+            const int freed = base;
             top -= kChunk;
-            em_cur = em_nxt;
+            off -= kChunk;
+            base += kChunk;
+            base -= (base >= RING) ? RING : 0;
+            em >>= 32;
             cp_async_wait<0>();
             __syncwarp();
-            em_nxt = chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + ((cur + 1) % 3) * kChunk * R);
-            chunk_copy<C>(r, top - 2 * kChunk, bufs + freed * kChunk * R);
+            int nxt = base + kChunk;
+            nxt -= (nxt >= RING) ? RING : 0;
+            em |= (unsigned long long)chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + nxt * R) << 32;
+            chunk_copy<C>(r, top - 2 * kChunk, bufs + freed * R);
         }
-        const int off = top - bb;
-        const int j = le - e;
-        if (j < 0 || j >= r.W) {
-            status = -1;
-            break;
-        }
-        const uint32_t *rec = bufs + cur * kChunk * R + off * R + 2 * (j % C);
-        const uint2 wv = *reinterpret_cast<const uint2 *>(rec);
-        const unsigned bit = (unsigned)(j / C);
-        if (lane == (n & 31)) mine = make_int2(e, k);
-        n++;
-        if ((n & 31) == 0) {                    // pairs n-32 .. n-1 -> out[cap-n .. cap-n+31]
-            const int t = n - 32 + lane;
-            if (t < cap) out[cap - 1 - t] = mine;
-        }
-        const unsigned long long em = (unsigned long long)em_cur | ((unsigned long long)em_nxt << 32);
-        const int emove_b = (int)((em >> off) & 1ull);           // band bb moved by an event
-        if ((wv.y >> bit) & 1u) {                                // L
-            k--;
-            le -= emove_b;
-        } else if ((wv.x >> bit) & 1u) {                         // U
-            e--;
-            le -= emove_b;
-        } else {                                                 // D
-            e--;
-            k--;
-            le -= emove_b + (int)((em >> (off + 1)) & 1ull);
-        }
-        bb = e + k + 2;
     }
     cp_async_wait<0>();
     __syncwarp();
-    const int rest = n & 31;
-    if (rest) {
-        const int t = n - rest + lane;
-        if (lane < rest && t < cap) out[cap - 1 - t] = mine;
-    }
     n_out = n;
-    return status;
+    return bad ? -1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -811,7 +799,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 }
 
 template <int C, bool MIXED, bool FULLW>
-__global__ void __launch_bounds__(kWarps * 32) align_kernel(const AlignArgs a)
+__global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(const AlignArgs a)
 {
     constexpr int R = Rec<C>::R;
     __shared__ __align__(16) uint32_t bt[kWarps][3 * kChunk * R];
