@@ -8,11 +8,13 @@ clipped to 500 b - 50 kb), k = 6, W = 100.  The metric is band-cell updates
 per second (GCUPS: in-matrix cells filled, summed over reads), also reported
 as reads/s.
 
-  value : device-resident inputs (abea_align_batch_device), CUDA events on
-          the library's stream around K back-to-back steps.
+  value : device-resident inputs (abea_align_batch_device); K steps spread
+          round-robin over D contexts, each on its own stream (D = 3 batches
+          in flight by default, so one batch's longest reads overlap the next
+          batches' work), CUDA events around all K steps.
   e2e   : the same metric through abea_align_packed with page-locked host
-          buffers; each step copies its inputs host->device and its results
-          device->host inside the timed region.
+          buffers, one host thread per context; each step copies its inputs
+          host->device and its results device->host inside the timed region.
 
 --impl reference runs the CPU oracle (oracle/, FP32) on bounded samples of
 the same workload.  With --gpus N > 1 each rank runs its own replica of the
@@ -36,12 +38,16 @@ WORKLOAD = "batch_4096_ln5kb"
 METRIC = "ABEA band-cell updates/s (GCUPS) and reads/s on 1 GB300; p50/p99 latency served"
 UNIT = "GCUPS"
 OPS_PER_CELL = 10   # FP32-pipe ops of the canonical cell: 2 FFMA, 4 FADD, 2 compare, 2 select
+# DRAM bytes (read + write) per band of the core kernel from one ncu capture
+# (profiles/align_kernel_1024reads_sections.md), valid only for the kernel
+# source it was taken on; scaled to a launch by the batch's bands.
+TRAFFIC_CAPTURE = {"source_sha1": "805c501b3761c6c655d7a8e3e3d66d3aa262be13", "bytes_per_band": 76.05}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
@@ -49,6 +55,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--depth", type=int, default=3, help="batches in flight (one context and stream each)")
+    p.add_argument("--block-theta", type=float, default=0.0,
+                   help="reads above this multiple of the even per-warp share of bands run on a whole block "
+                        "(<= 0: one warp per read)")
     return p.parse_args()
 
 
@@ -111,6 +121,17 @@ def measured_peaks():
         return {}
 
 
+def traffic_per_launch(bands: int):
+    """DRAM bytes of one core-kernel launch over `bands` bands, from the ncu capture; None once the
+    kernel source differs from the captured one."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2101_05012_gb300", "csrc", "abea_align.cu")
+    with open(src, "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != TRAFFIC_CAPTURE["source_sha1"]:
+            return None
+    return int(TRAFFIC_CAPTURE["bytes_per_band"] * bands)
+
+
 def oracle_rate(batch, seconds: float, threads: int):
     """FP32 oracle on a bounded, evenly spaced sample of the batch: (GCUPS, reads/s, sample text)."""
     from oracle import oracle
@@ -167,6 +188,9 @@ def run_reference(args):
 
 
 def run_ours(args):
+    import ctypes
+    import threading
+
     import torch
     import torch.distributed as dist
 
@@ -179,29 +203,52 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     batch = synth.make_batch(args.workload, n_reads=args.reads)
     n = batch.n
-    ctx = binding.Context(local_rank)
-    ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
+    D = max(1, args.depth)
     pair_off = binding.pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
+    n_pairs = int(pair_off[-1])
 
-    # device-resident inputs and outputs
+    # D contexts, each with its own stream and outputs; step i runs on context i % D, so up to D
+    # batches are in flight and one batch's last long reads overlap the next batches' work
+    ctxs = []
+    for _ in range(D):
+        c = binding.Context(local_rank)
+        c.set_model(batch.k, batch.model_mean, batch.model_stdv)
+        c.set_block_mode(args.block_theta)
+        ctxs.append(c)
     d_seq = torch.from_numpy(batch.seq).to(dev)
     d_ev = torch.from_numpy(batch.events).to(dev)
-    d_out = torch.zeros(n * 24, dtype=torch.uint8, device=dev)
-    d_pairs = torch.zeros(int(pair_off[-1]) * 2, dtype=torch.int32, device=dev)
-    stream = torch.cuda.Stream(dev)
+    d_out = [torch.zeros(n * 24, dtype=torch.uint8, device=dev) for _ in range(D)]
+    d_pairs = [torch.zeros(n_pairs * 2, dtype=torch.int32, device=dev) for _ in range(D)]
+    streams = [torch.cuda.Stream(dev) for _ in range(D)]
+    main = torch.cuda.Stream(dev)
 
-    def step():
-        ctx.align_batch_device(n, batch.W, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out,
-                               d_pairs, pair_off, stream=stream.cuda_stream)
+    def step(i):
+        j = i % D
+        ctxs[j].align_batch_device(n, batch.W, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out[j],
+                                   d_pairs[j], pair_off, stream=streams[j].cuda_stream)
 
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
-    res = binding.results_from_bytes(d_out.cpu().numpy())
+    for i in range(max(args.warmup, D)):
+        step(i)
+    torch.cuda.synchronize(dev)
+    res = binding.results_from_bytes(d_out[0].cpu().numpy())
     if not np.all(res["status"] == 0):
         raise SystemExit(f"bench: {int(np.sum(res['status'] != 0))} reads failed")
+    for j in range(1, D):
+        if not np.array_equal(binding.results_from_bytes(d_out[j].cpu().numpy()), res):
+            raise SystemExit("bench: contexts disagree")
     cells = int(res["cells"].sum())
-    ctx.last_launch_stats()                      # reset the launch counters
+
+    # one batch at a time (latency of a batch; not the headline)
+    lat = []
+    for _ in range(3):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(streams[0])
+        step(0)
+        a1.record(streams[0])
+        a1.synchronize()
+        lat.append(a0.elapsed_time(a1))
+    for c in ctxs:
+        c.last_launch_stats()                    # reset the launch counters
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -209,14 +256,24 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local_rank)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    e0.record(main)
+    for st in streams:
+        st.wait_event(e0)
+    for i in range(args.steps):
+        step(i)
+    for st in streams:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        main.wait_event(ev)
+    e1.record(main)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
-    launches, align_ms = ctx.last_launch_stats()
+    launches, align_ms = 0, 0.0
+    for c in ctxs:
+        nl, ms = c.last_launch_stats()
+        launches += nl
+        align_ms += ms
     if world > 1:
         dist.barrier()
         t = torch.tensor([ms_total], device=dev)
@@ -226,54 +283,76 @@ def run_ours(args):
     value = world * cells * args.steps / (ms_total / 1e3) / 1e9
     reads_per_s = world * n * args.steps / (ms_total / 1e3)
 
-    # end to end through the host-memory call, page-locked host buffers
+    # end to end through the host-memory call (abea_align_packed, page-locked host buffers): one host
+    # thread per context, each call copies its inputs in and its results out
     e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     h_seq, h_ev = pin(batch.seq), pin(batch.events)
-    h_out = torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy()
-    h_pairs = torch.zeros(int(pair_off[-1]) * 2, dtype=torch.int32).pin_memory().numpy()
-    import ctypes
+    h_out = [torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy() for _ in range(D)]
+    h_pairs = [torch.zeros(n_pairs * 2, dtype=torch.int32).pin_memory().numpy() for _ in range(D)]
     sc = np.ascontiguousarray(batch.scalings, np.float32)
+    errors = []
 
-    def e2e_step():
-        rc = ctx.lib.abea_align_packed(ctx.h, n, batch.W, binding._p(h_seq), binding._p(batch.seq_off),
-                                       binding._p(h_ev), binding._p(batch.ev_off), binding._p(sc),
-                                       binding._p(h_out), binding._p(h_pairs), binding._p(pair_off),
-                                       ctypes.c_void_p(stream.cuda_stream))
+    def e2e_step(j):
+        c = ctxs[j]
+        rc = c.lib.abea_align_packed(c.h, n, batch.W, binding._p(h_seq), binding._p(batch.seq_off),
+                                     binding._p(h_ev), binding._p(batch.ev_off), binding._p(sc),
+                                     binding._p(h_out[j]), binding._p(h_pairs[j]), binding._p(pair_off),
+                                     ctypes.c_void_p(streams[j].cuda_stream))
         if rc != 0:
-            raise binding.AbeaError(rc, "abea_align_packed")
+            errors.append(rc)
 
-    e2e_step()
-    ctx.last_launch_stats()
+    for j in range(D):
+        e2e_step(j)
+    for c in ctxs:
+        c.last_launch_stats()
+    gate = threading.Barrier(D + 1)
+
+    def worker(j):
+        gate.wait()
+        for _ in range(j, e2e_steps, D):
+            e2e_step(j)
+
+    threads = [threading.Thread(target=worker, args=(j,)) for j in range(D)]
+    for th in threads:
+        th.start()
     if world > 1:
         dist.barrier()
+    gate.wait()
     t = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
+    for th in threads:
+        th.join()
     e2e_s = time.perf_counter() - t
-    e2e_launches, _ = ctx.last_launch_stats()
+    if errors:
+        raise binding.AbeaError(errors[0], "abea_align_packed")
+    e2e_launches = sum(c.last_launch_stats()[0] for c in ctxs)
     if world > 1:
         tt = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    r2 = binding.results_from_bytes(h_out)
-    if not np.array_equal(r2, res):
-        raise SystemExit("bench: host-memory results differ from device-resident results")
+    for j in range(D):
+        if not np.array_equal(binding.results_from_bytes(h_out[j]), res):
+            raise SystemExit("bench: host-memory results differ from device-resident results")
     e2e_value = world * cells * e2e_steps / e2e_s / 1e9
     h2d = int(batch.seq.nbytes + batch.events.nbytes + n * (112 + 4))
     d2h = int(n * 24 + (pair_off[-1] - pair_off[0]) * 8)
 
-    # roofline of the core kernel: FP32-pipe issue
+    # roofline of the core kernel (98 % of device time): FP32-pipe issue.  With D batches in flight
+    # the launches overlap; the kernel's rate is the cells of one launch over the launch period
+    # (timed region / launches); the mean span of a single launch is reported beside it.
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
-    align_ms_launch = align_ms / max(args.steps, 1)
-    achieved = cells * OPS_PER_CELL / (align_ms_launch / 1e3) / 1e12
+    span_ms = align_ms / max(args.steps, 1)
+    period_ms = ms_total / max(args.steps, 1)
+    achieved = cells * OPS_PER_CELL / (period_ms / 1e3) / 1e12
     peak = sms * 128 * sm_max * 1e6 / 1e12
+    bands = int((batch.n_events() + batch.n_kmers() + 1).sum())
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "kernel": "align_kernel<4,false>", "per_launch_ms": align_ms_launch,
+                "traffic": traffic_per_launch(bands),
+                "kernel": "align_kernel<4,false,false,1>", "launch_period_ms": period_ms,
+                "launch_span_ms": span_ms, "batches_in_flight": D,
                 "ops_per_cell": OPS_PER_CELL,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)"}
     if clk and clk.get("sm_mhz"):
@@ -281,9 +360,9 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        gc, rps, desc = oracle_rate(batch, args.cpu_seconds, threads)
-        cpu = {"value": gc, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc, "reads_per_s": rps}
+        threads_n = os.cpu_count() or 1
+        gc, rps, desc = oracle_rate(batch, args.cpu_seconds, threads_n)
+        cpu = {"value": gc, "unit": UNIT, "cores": threads_n, "kind": "oracle", "sample": desc, "reads_per_s": rps}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -293,14 +372,17 @@ def run_ours(args):
                            "cells_per_step": cells, "bases_per_step": int(batch.seq.size),
                            "events_per_step": int(batch.events.size),
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "batches_in_flight": D, "block_theta": args.block_theta,
                            "l2": "inputs (195 MB events) and outputs (2.4 GB trace per step) exceed the 129 MB L2"},
-                "reads_per_s": reads_per_s, "kernel_gcups": cells / (align_ms_launch / 1e3) / 1e9,
-                "gpu_launches": launches,
+                "reads_per_s": reads_per_s, "batch_latency_ms": statistics.median(lat),
+                "kernel_launch_span_ms": span_ms, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches},
+                        "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
+                        "host_threads": D},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -148,6 +148,18 @@ int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
  * between two calls (later ones are folded into the last slot). */
 int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
 
+/* Scheduling of long reads (the paper has no counterpart; results do not
+ * depend on it).  Within one core-kernel launch a read normally occupies one
+ * warp; a read with more than theta times the bands that each warp of the
+ * launch would get if the batch were spread evenly is instead shared by the
+ * four warps of one block (at most one such read per block, longest first),
+ * so that it does not set the batch's makespan.  theta <= 0 disables this;
+ * the default is 1.0.  Band widths that do not split over four warps
+ * (W < 32, W not a multiple of 4, or W / 4 not a multiple of 1 or 2 with
+ * at most 31 lanes) always run one read per warp.  Returns ABEA_ERR_ARG for
+ * a NaN theta. */
+int abea_set_block_mode(abea_ctx *ctx, double theta);
+
 /* The paper has no counterpart to this call.  abea_align_batch_device without
  * any memory allocation, for callers that cannot call cudaMalloc: for
  * example a plugin inside a host application that already holds (nearly)

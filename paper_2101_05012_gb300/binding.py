@@ -28,7 +28,7 @@ READ_OK, READ_FAIL_NO_END, READ_BAD_INPUT, READ_CAPACITY = range(4)
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
-           "abea_align_batch_device_noalloc"]
+           "abea_set_block_mode", "abea_align_batch_device_noalloc"]
 
 
 class Scalings(ctypes.Structure):
@@ -82,6 +82,7 @@ def load(path: Optional[str] = None):
     lib.abea_align_packed.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_align_batch_device.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.abea_set_block_mode.argtypes = [P, ctypes.c_double]
     lib.abea_align_batch_device_noalloc.argtypes = [ctypes.c_int, P, P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     for f in EXPORTS:
         if f not in ("abea_destroy", "abea_strerror"):
@@ -197,6 +198,10 @@ class Context:
             self.h, n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
             _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
             ctypes.c_void_p(stream)), "abea_align_batch_device")
+
+    def set_block_mode(self, theta: float):
+        """Reads above theta x the even per-warp share of bands run on a whole block (<= 0: never)."""
+        _check(self.lib.abea_set_block_mode(self.h, float(theta)), "abea_set_block_mode")
 
     def last_launch_stats(self):
         n = ctypes.c_int32()

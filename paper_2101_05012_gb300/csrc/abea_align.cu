@@ -60,6 +60,7 @@
 //   l = left + lp_skip; S = (l > s) ? l : s
 // (max(diag+lp_step+E, up+lp_stay+E) = max(diag+lp_step, up+lp_stay) + E
 // because rounding is monotone), plus the exact renormalisation below.
+#include <algorithm>
 #include <climits>
 
 #include "abea_internal.h"
@@ -118,6 +119,7 @@ template <int C>
 struct Lane {
     float X[C], A[C], B[C], Cc[C];   // operands of the lane's offsets
     float qprev;                     // boundary value of the previous band's shifted view
+    float nb_lo, nb_hi;              // block mode: S_b of the neighbour warps at offsets off0-1 and off0+W'
     bool kprev;                      // the last band moved by one k-mer
     bool knext;                      // the next band moves by one k-mer (decided)
     int ll_e, ll_k;                  // offset-0 cell of the last computed band
@@ -145,12 +147,17 @@ struct ReadCtx {
     unsigned dead_mask;              // slots of this lane beyond offset W-1
     float lsk;                       // lp_skip; -inf above the band
     Consts cs;
+    // block mode (the block's warps share one read; warp gw owns offsets
+    // [off0, off0 + W') of every band, W' = W / kWarps)
+    int off0, gw;
+    float2 *xch;                     // [2][kWarps] band edges (S at off0, S at off0+W'-1), by band parity
+    float *rx;                       // [kWarps] renormalisation maxima
 };
 
 // Band b from S_{b-1} (P) and S_{b-2} (PP); S_b is written into PP and its
 // trace words into w.  KM: this band moves by one k-mer; KP: the previous
 // band did.  FULLW: all 32 lanes are live (no lane above the band).
-template <int C, bool KM, bool KP, bool FULLW>
+template <int C, bool KM, bool KP, bool FULLW, bool GROUP>
 __device__ __forceinline__ void band_fill(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C],
                                           uint32_t (&w)[2 * C])
 {
@@ -175,14 +182,17 @@ __device__ __forceinline__ void band_fill(Lane<C> &s, const ReadCtx &r, float (&
     }
     // Q[t] = S_{b-1}[C*lane + t - 1 + KM], t = 0..C: left of slot i is Q[i],
     // up is Q[i+1].  Across the band's edges the neighbour lane is a lane
-    // above the band (all -inf), unless FULLW.
+    // above the band (all -inf), unless FULLW; in block mode the value across
+    // the warp's edge comes from the neighbour warp.
     float qb;
     if (KM) {
         qb = __shfl_down_sync(kFull, P[0], 1);
         if (FULLW && r.last_lane) qb = neg_inf();
+        if (GROUP && r.last_lane) qb = s.nb_hi;
     } else {
         qb = __shfl_sync(kFull, P[C - 1], r.src_up);
         if (FULLW && r.first_lane) qb = neg_inf();
+        if (GROUP && r.first_lane) qb = s.nb_lo;
     }
     float S[C];
 #pragma unroll
@@ -204,17 +214,39 @@ __device__ __forceinline__ void band_fill(Lane<C> &s, const ReadCtx &r, float (&
     s.qprev = qb;
 }
 
-template <int C, bool FULLW>
+template <int C, bool FULLW, bool GROUP>
 __device__ __forceinline__ void band_fill_dispatch(bool K, Lane<C> &s, const ReadCtx &r, float (&P)[C],
                                                    float (&PP)[C], uint32_t (&w)[2 * C])
 {
     if (K) {
-        if (s.kprev) band_fill<C, true, true, FULLW>(s, r, P, PP, w);
-        else band_fill<C, true, false, FULLW>(s, r, P, PP, w);
+        if (s.kprev) band_fill<C, true, true, FULLW, GROUP>(s, r, P, PP, w);
+        else band_fill<C, true, false, FULLW, GROUP>(s, r, P, PP, w);
     } else {
-        if (s.kprev) band_fill<C, false, true, FULLW>(s, r, P, PP, w);
-        else band_fill<C, false, false, FULLW>(s, r, P, PP, w);
+        if (s.kprev) band_fill<C, false, true, FULLW, GROUP>(s, r, P, PP, w);
+        else band_fill<C, false, false, FULLW, GROUP>(s, r, P, PP, w);
     }
+}
+
+// Block mode: barrier over the block's warps (all of them share the read).
+__device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kWarps * 32) : "memory"); }
+
+// Block mode: publish band b's edge cells (S = S_b), wait for the other warps,
+// then read the band's end cells (offsets 0 and W-1) and the neighbour
+// warps' edges for the next band.  Slots alternate by band parity, so one
+// barrier per band suffices: a slot is rewritten two bands later, after
+// every warp has passed the barrier that follows its reads.
+template <int C>
+__device__ __forceinline__ void group_exchange(Lane<C> &s, const ReadCtx &r, int b, const float (&S)[C], float &lo,
+                                               float &hi)
+{
+    float2 *x = r.xch + (b & 1) * kWarps;
+    if (r.first_lane) x[r.gw].x = S[0];
+    if (r.last_lane) x[r.gw].y = S[C - 1];
+    group_sync();
+    lo = x[0].x;
+    hi = x[kWarps - 1].y;
+    s.nb_lo = (r.gw > 0) ? x[r.gw > 0 ? r.gw - 1 : 0].y : neg_inf();
+    s.nb_hi = (r.gw < kWarps - 1) ? x[r.gw < kWarps - 1 ? r.gw + 1 : 0].x : neg_inf();
 }
 
 // The value of a band at offset W-1.
@@ -238,7 +270,7 @@ __device__ __forceinline__ float far_end(const ReadCtx &r, const float (&S)[C])
 // running scores small so that later FP32 additions round at a fine ulp
 // instead of drifting on long reads.  The total shift is kept in FP64 and
 // added back to the end score.  The FP32 oracle applies the same shifts.
-template <int C>
+template <int C, bool GROUP>
 __device__ __forceinline__ void renormalise(Lane<C> &s, const ReadCtx &r, float (&Sb)[C], float (&Sb1)[C])
 {
     float m = neg_inf();
@@ -249,6 +281,12 @@ __device__ __forceinline__ void renormalise(Lane<C> &s, const ReadCtx &r, float 
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+    if (GROUP) {                       // the maximum over the whole band
+        if (r.first_lane) r.rx[r.gw] = m;
+        group_sync();
+#pragma unroll
+        for (int g = 0; g < kWarps; g++) m = fmaxf(m, r.rx[g]);
+    }
     if (m <= -2048.0f) {
         const float R = -1024.0f * floorf(__fmul_rn(-m, 1.0f / 1024.0f));
 #pragma unroll
@@ -257,6 +295,10 @@ __device__ __forceinline__ void renormalise(Lane<C> &s, const ReadCtx &r, float 
             Sb1[i] = __fsub_rn(Sb1[i], R);
         }
         s.qprev = __fsub_rn(s.qprev, R);
+        if (GROUP) {                   // the neighbours' edges of S_b, shifted by their own warps too
+            s.nb_lo = __fsub_rn(s.nb_lo, R);
+            s.nb_hi = __fsub_rn(s.nb_hi, R);
+        }
         s.frame += (double)R;
     }
 }
@@ -294,19 +336,23 @@ __device__ __forceinline__ void next_kmer(Lane<C> &s, const ReadCtx &r, int k)
 // The move of band b+1 from band b's end cells (S = S_b, s.b = b).
 // GENERAL: band b may reach beyond the last k-mer, whose cells are not -inf
 // in registers.
+// The move rule on band b's end cells lo = S_b[0], hi = S_b[W-1] (s.b = b):
+// cells beyond the last k-mer count as -inf; both -inf: a k-mer move on odd
+// bands.
+template <int C>
+__device__ __forceinline__ bool general_move(const Lane<C> &s, const ReadCtx &r, float lo, float hi)
+{
+    if (s.ll_k >= r.n_k) lo = neg_inf();
+    if (s.ll_k + r.W - 1 >= r.n_k) hi = neg_inf();
+    return (lo == neg_inf() && hi == neg_inf()) ? (((s.b + 1) & 1) != 0) : (lo < hi);
+}
+
 template <int C, bool MIXED, bool GENERAL>
 __device__ __forceinline__ void decide_next(Lane<C> &s, const ReadCtx &r, const float (&S)[C])
 {
     float lo = __shfl_sync(kFull, S[0], 0);
     float hi = far_end<C, MIXED>(r, S);
-    bool k;
-    if (GENERAL) {
-        if (s.ll_k >= r.n_k) lo = neg_inf();
-        if (s.ll_k + r.W - 1 >= r.n_k) hi = neg_inf();
-        k = (lo == neg_inf() && hi == neg_inf()) ? (((s.b + 1) & 1) != 0) : (lo < hi);
-    } else {
-        k = lo < hi;
-    }
+    const bool k = GENERAL ? general_move<C>(s, r, lo, hi) : (lo < hi);
     s.knext = __all_sync(kFull, k);
 }
 
@@ -339,15 +385,30 @@ __device__ __forceinline__ void store_record(const ReadCtx &r, int b, const uint
     }
 }
 
+// Block mode: lane 0 of warp gw writes its 2C words of band b's record
+// (words [2C*gw, 2C*gw + 2C) of a record of kWarps*2C words).
+template <int C>
+__device__ __forceinline__ void store_record_group(const ReadCtx &r, int b, const uint32_t (&w)[2 * C])
+{
+    constexpr int RG = 2 * C * kWarps;
+    uint32_t *dst = r.tr + (size_t)b * RG + 2 * C * r.gw;
+#pragma unroll
+    for (int q = 0; q < C; q++)
+        asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, %3, 0;\n"
+                     " @p st.global.v2.b32 [%0], {%1,%2};\n}\n" ::"l"(dst + 2 * q),
+                     "r"(w[2 * q]), "r"(w[2 * q + 1]), "r"(r.lane)
+                     : "memory");
+}
+
 // One band b = s.b: fill with the decided move, checks (GENERAL), trace
 // record, decision for band b+1, prefetch.
-template <int C, bool MIXED, bool FULLW, bool GENERAL>
+template <int C, bool MIXED, bool FULLW, bool GENERAL, bool GROUP>
 __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
 {
     const int b = s.b;
     const bool K = s.knext;
     uint32_t w[2 * C];
-    band_fill_dispatch<C, FULLW>(K, s, r, P, PP, w);
+    band_fill_dispatch<C, FULLW, GROUP>(K, s, r, P, PP, w);
     s.kprev = K;
     if (K) s.ll_k++;
     else s.ll_e++;
@@ -364,7 +425,7 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
             const float v = (e >= 0 && e < r.n_e) ? __fmul_rn((float)(e + 1), r.cs.lp_trim) : neg_inf();
 #pragma unroll
             for (int i = 0; i < C; i++)
-                if (C * r.lane + i == jt) PP[i] = v;
+                if ((GROUP ? r.off0 : 0) + C * r.lane + i == jt && (!GROUP || r.lane < r.L)) PP[i] = v;
         }
         // end cell candidates: (e, n_k-1) plus the n_e-1-e trailing events trimmed
         const int jend = r.n_k - 1 - s.ll_k;
@@ -373,7 +434,7 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
             if (e >= 0 && e < r.n_e) {
 #pragma unroll
                 for (int i = 0; i < C; i++) {
-                    if (C * r.lane + i == jend) {
+                    if ((GROUP ? r.off0 : 0) + C * r.lane + i == jend && (!GROUP || r.lane < r.L)) {
                         const float rel = __fadd_rn(PP[i], __fmul_rn((float)(r.n_e - 1 - e), r.cs.lp_trim));
                         const double cand = s.frame + (double)rel;
                         if (cand > s.best) {
@@ -389,11 +450,20 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
         const int jhi = min(r.W, min(s.ll_e + 1, r.n_k - s.ll_k));
         s.cells += max(0, jhi - jlo);
     }
-    decide_next<C, MIXED, GENERAL>(s, r, PP);
-    store_record<C>(r, b, w);
-    if (FULLW && r.lane == 0) r.mv[b] = K ? 1 : 0;
-    if (K) next_kmer(s, r, s.ll_k + r.Wp);
-    else next_event(s, r, s.ll_e + 1);
+    if (GROUP) {
+        float lo, hi;
+        group_exchange<C>(s, r, b, PP, lo, hi);
+        s.knext = GENERAL ? general_move<C>(s, r, lo, hi) : (lo < hi);
+        store_record_group<C>(r, b, w);
+        if (K) next_kmer(s, r, s.ll_k + r.off0 + r.Wp);
+        else next_event(s, r, s.ll_e + 1 - r.off0);
+    } else {
+        decide_next<C, MIXED, GENERAL>(s, r, PP);
+        store_record<C>(r, b, w);
+        if (FULLW && r.lane == 0) r.mv[b] = K ? 1 : 0;
+        if (K) next_kmer(s, r, s.ll_k + r.Wp);
+        else next_event(s, r, s.ll_e + 1);
+    }
     s.b = b + 1;
 }
 
@@ -428,10 +498,24 @@ __device__ __forceinline__ int lean_run(const Lane<C> &s, const ReadCtx &r)
 // registers and the injected operand, and their shuffles are issued before
 // the rest of the band; the same values come out of the full band, so the
 // decision is unchanged.
-template <int C, bool MIXED, bool FULLW, bool KM, bool KP>
+template <int C, bool MIXED, bool FULLW, bool KM, bool KP, bool GROUP>
 __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
 {
     const int b = s.b;
+    if (GROUP) {                       // block mode: the end cells come through shared memory
+        uint32_t w[2 * C];
+        band_fill<C, KM, KP, false, true>(s, r, P, PP, w);
+        if (KM) s.ll_k++;
+        else s.ll_e++;
+        float lo, hi;
+        group_exchange<C>(s, r, b, PP, lo, hi);
+        s.knext = lo < hi;
+        store_record_group<C>(r, b, w);
+        if (KM) next_kmer(s, r, s.ll_k + r.off0 + r.Wp);
+        else next_event(s, r, s.ll_e + 1 - r.off0);
+        s.b = b + 1;
+        return;
+    }
     float lo_src, hi_src;
     if (!MIXED) {
         const float lp_step = r.cs.lp_step, lp_stay = r.cs.lp_stay, lsk = r.lsk;
@@ -463,7 +547,7 @@ __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&
         }
     }
     uint32_t w[2 * C];
-    band_fill<C, KM, KP, FULLW>(s, r, P, PP, w);
+    band_fill<C, KM, KP, FULLW, false>(s, r, P, PP, w);
     if (MIXED) {
 #pragma unroll
         for (int i = 0; i < C; i++)
@@ -490,45 +574,45 @@ __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&
 // m lean bands (m >= 1) as a state machine over (which array holds S_{b-1},
 // previous move); each state branches once, on the decided move.  On exit
 // P holds the last band and PP the one before.
-template <int C, bool MIXED, bool FULLW>
+template <int C, bool MIXED, bool FULLW, bool GROUP>
 __device__ __forceinline__ void lean_loop(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C], int m)
 {
     if (s.kprev) goto p0_k1;
     goto p0_k0;
 p0_k0:
     if (s.knext) {
-        lean_band<C, MIXED, FULLW, true, false>(s, r, P, PP);
+        lean_band<C, MIXED, FULLW, true, false, GROUP>(s, r, P, PP);
         if (--m == 0) goto out1_k1;
         goto p1_k1;
     }
-    lean_band<C, MIXED, FULLW, false, false>(s, r, P, PP);
+    lean_band<C, MIXED, FULLW, false, false, GROUP>(s, r, P, PP);
     if (--m == 0) goto out1_k0;
     goto p1_k0;
 p0_k1:
     if (s.knext) {
-        lean_band<C, MIXED, FULLW, true, true>(s, r, P, PP);
+        lean_band<C, MIXED, FULLW, true, true, GROUP>(s, r, P, PP);
         if (--m == 0) goto out1_k1;
         goto p1_k1;
     }
-    lean_band<C, MIXED, FULLW, false, true>(s, r, P, PP);
+    lean_band<C, MIXED, FULLW, false, true, GROUP>(s, r, P, PP);
     if (--m == 0) goto out1_k0;
     goto p1_k0;
 p1_k0:
     if (s.knext) {
-        lean_band<C, MIXED, FULLW, true, false>(s, r, PP, P);
+        lean_band<C, MIXED, FULLW, true, false, GROUP>(s, r, PP, P);
         if (--m == 0) goto out0_k1;
         goto p0_k1;
     }
-    lean_band<C, MIXED, FULLW, false, false>(s, r, PP, P);
+    lean_band<C, MIXED, FULLW, false, false, GROUP>(s, r, PP, P);
     if (--m == 0) goto out0_k0;
     goto p0_k0;
 p1_k1:
     if (s.knext) {
-        lean_band<C, MIXED, FULLW, true, true>(s, r, PP, P);
+        lean_band<C, MIXED, FULLW, true, true, GROUP>(s, r, PP, P);
         if (--m == 0) goto out0_k1;
         goto p0_k1;
     }
-    lean_band<C, MIXED, FULLW, false, true>(s, r, PP, P);
+    lean_band<C, MIXED, FULLW, false, true, GROUP>(s, r, PP, P);
     if (--m == 0) goto out0_k0;
     goto p0_k0;
 out1_k0:
@@ -547,7 +631,7 @@ out0_k1:
     return;
 }
 
-template <int C, bool MIXED, bool FULLW>
+template <int C, bool MIXED, bool FULLW, bool GROUP>
 __device__ __forceinline__ void band_loop(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
 {
     const int b_end = r.n_e + r.n_k;
@@ -560,11 +644,11 @@ __device__ __forceinline__ void band_loop(Lane<C> &s, const ReadCtx &r, float (&
                 const int to_renorm = (kRenormPeriod - (s.b % kRenormPeriod)) % kRenormPeriod + 1;
                 const int m = min(n, to_renorm);
                 n -= m;
-                lean_loop<C, MIXED, FULLW>(s, r, P, PP, m);
-                if (((s.b - 1) % kRenormPeriod) == 0) renormalise<C>(s, r, P, PP);
+                lean_loop<C, MIXED, FULLW, GROUP>(s, r, P, PP, m);
+                if (((s.b - 1) % kRenormPeriod) == 0) renormalise<C, GROUP>(s, r, P, PP);
             }
         } else {
-            band_step<C, MIXED, FULLW, true>(s, r, P, PP);
+            band_step<C, MIXED, FULLW, true, GROUP>(s, r, P, PP);
             swap_bands(P, PP);
         }
     }
@@ -582,11 +666,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Copy the trace records of bands top-lane (lane = 0..31) into buf.
-template <int C>
+// Copy the trace records (R words each) of bands top-lane (lane = 0..31)
+// into buf.
+template <int R>
 __device__ __forceinline__ void chunk_copy(const ReadCtx &r, int top, uint32_t *buf)
 {
-    constexpr int R = Rec<C>::R;
     const int mb = top - r.lane;
     if (mb >= 2) {                         // bands 0 and 1 hold no matrix cell
         const uint32_t *src = r.tr + (size_t)mb * R;
@@ -598,10 +682,9 @@ __device__ __forceinline__ void chunk_copy(const ReadCtx &r, int top, uint32_t *
 }
 
 // Bit l set: band top-l moved by one event.
-template <int C, bool FULLW>
+template <int R, bool FULLW>
 __device__ __forceinline__ unsigned chunk_event_moves(const ReadCtx &r, int top, const uint32_t *buf)
 {
-    constexpr int R = Rec<C>::R;
     const int mb = top - r.lane;
     bool kmove = false;
     if (mb >= 2) kmove = FULLW ? (r.mv[mb] != 0) : (((buf[r.lane * R] >> 31) & 1u) != 0);
@@ -615,22 +698,25 @@ __device__ __forceinline__ unsigned chunk_event_moves(const ReadCtx &r, int top,
 // sit in a shared-memory ring of three 32-band chunks, the next two always
 // on their way (cp.async); the band moves of the current and next chunk are
 // kept as one 64-bit word, so a step needs one shared-memory load.
-template <int C, bool FULLW>
-__device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end, int2 *out, int cap, int &n_out)
+// Record layout: per-warp mode, offset j is bit j/C of word pair j%C of a
+// record of R words; block mode (GROUP), offset j = gw*W' + C*lane + i is
+// bit lane of word pair gw*C + i, W' = wg (wg_magic = ceil(2^32 / wg)).
+template <int C, int R, bool FULLW, bool GROUP>
+__device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end, int2 *out, int cap, int &n_out,
+                         unsigned wg = 1, unsigned wg_magic = 0)
 {
-    constexpr int R = Rec<C>::R;
     constexpr int RING = 3 * kChunk;
     int e = e_end, k = r.n_k - 1;
     int top = e + k + 2;               // band held in ring slot `base`
     int base = 0;
-    chunk_copy<C>(r, top, bufs);
-    chunk_copy<C>(r, top - kChunk, bufs + kChunk * R);
-    chunk_copy<C>(r, top - 2 * kChunk, bufs + 2 * kChunk * R);
+    chunk_copy<R>(r, top, bufs);
+    chunk_copy<R>(r, top - kChunk, bufs + kChunk * R);
+    chunk_copy<R>(r, top - 2 * kChunk, bufs + 2 * kChunk * R);
     cp_async_wait<1>();
     __syncwarp();
     // bit i: band top-i moved by one event
-    unsigned long long em = (unsigned long long)chunk_event_moves<C, FULLW>(r, top, bufs) |
-                            ((unsigned long long)chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + kChunk * R)
+    unsigned long long em = (unsigned long long)chunk_event_moves<R, FULLW>(r, top, bufs) |
+                            ((unsigned long long)chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + kChunk * R)
                              << 32);
     const bool writer = r.lane == 0;
     int le = le_end;
@@ -642,8 +728,18 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
         bad = (unsigned)j >= (unsigned)r.W ? 1u : 0u;
         int p = base + off;
         p -= (p >= RING) ? RING : 0;
-        const uint2 w = *reinterpret_cast<const uint2 *>(bufs + p * R + 2 * ((unsigned)j % C));
-        const unsigned bit = (unsigned)j / C;
+        unsigned pair, bit;
+        if (GROUP) {
+            const unsigned ju = bad ? 0u : (unsigned)j;          // keeps the load inside the record
+            const unsigned gq = __umulhi(ju, wg_magic);          // ju / wg
+            const unsigned jj = ju - gq * wg;
+            pair = gq * C + jj % C;
+            bit = jj / C;
+        } else {
+            pair = (unsigned)j % C;
+            bit = (unsigned)j / C;
+        }
+        const uint2 w = *reinterpret_cast<const uint2 *>(bufs + p * R + 2 * pair);
         if (writer && n < cap) out[cap - 1 - n] = make_int2(e, k);
         n++;
         const unsigned l = (w.y >> bit) & 1u;
@@ -665,8 +761,8 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
             __syncwarp();
             int nxt = base + kChunk;
             nxt -= (nxt >= RING) ? RING : 0;
-            em |= (unsigned long long)chunk_event_moves<C, FULLW>(r, top - kChunk, bufs + nxt * R) << 32;
-            chunk_copy<C>(r, top - 2 * kChunk, bufs + freed * R);
+            em |= (unsigned long long)chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + nxt * R) << 32;
+            chunk_copy<R>(r, top - 2 * kChunk, bufs + freed * R);
         }
     }
     cp_async_wait<0>();
@@ -676,6 +772,20 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
 }
 
 // ---------------------------------------------------------------------------
+
+// Pairs (cap - n .. cap-1 of out) moved to the front, ascending, by the warp.
+__device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lane)
+{
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int t = base + lane;
+        int2 v = make_int2(0, 0);
+        if (t < n) v = out[cap - n + t];
+        __syncwarp();
+        if (t < n) out[t] = v;
+        __syncwarp();
+    }
+}
 
 template <int C, bool MIXED, bool FULLW>
 __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int lane, uint32_t *bt_bufs)
@@ -743,7 +853,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     s.cells = 0;
     s.lean_bands = 0;
 
-    band_loop<C, MIXED, FULLW>(s, r, P, PP);
+    band_loop<C, MIXED, FULLW, false>(s, r, P, PP);
 
     // end cell: max score, then smallest event (the first maximum in event order)
     double best = s.best;
@@ -769,22 +879,14 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
         status = ABEA_READ_FAIL_NO_END;
     } else {
         __syncwarp();                         // lane 0's trace stores are visible to the warp
-        const int rc = backtrack<C, FULLW>(r, bt_bufs, best_e, best_le, out, cap, n);
+        const int rc = backtrack<C, Rec<C>::R, FULLW, false>(r, bt_bufs, best_e, best_le, out, cap, n);
         if (rc != 0) {
             status = ABEA_READ_FAIL_NO_END;   // internal inconsistency, reported as no alignment
             n = 0;
         } else if (n > cap) {
             status = ABEA_READ_CAPACITY;
         } else {
-            __syncwarp();
-            for (int base = 0; base < n; base += 32) {   // move the pairs to the front, ascending
-                const int t = base + lane;
-                int2 v = make_int2(0, 0);
-                if (t < n) v = out[cap - n + t];
-                __syncwarp();
-                if (t < n) out[t] = v;
-                __syncwarp();
-            }
+            compact_pairs(out, cap, n, lane);
         }
     }
     if (lane == 0) {
@@ -798,17 +900,196 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     }
 }
 
-template <int C, bool MIXED, bool FULLW>
+// Shared state of block mode.
+struct GroupShared {
+    float2 xch[2][kWarps];
+    float rx[kWarps];
+    double best[kWarps];
+    int best_e[kWarps], best_le[kWarps];
+};
+
+// Block mode: the kWarps warps of the block align one read together (a long
+// one, so that it does not set the batch's makespan).  Warp gw owns offsets
+// [gw*W', gw*W' + W') of every band, W' = W / kWarps = C * L'; the two cells
+// next to a warp's edge and the band's two end cells come through shared
+// memory after each band (one barrier).  Every warp runs the same bands in
+// the same order: the moves are read by all of them from the same shared
+// values, so they all pass the same barriers.  Warp 0 then walks the trace
+// alone; the other warps return to per-warp work.  Record: kWarps*2C words
+// per band.  Results equal those of the per-warp mode bit for bit (same
+// cells, same operations).
+// Out of line: inlined into the kernel, this code slows the per-warp loop by
+// about a fifth under full load (measured); its shared memory is its own, so
+// it is addressed as shared memory here.
+template <int C>
+__device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc &d, int rid, int warp, int lane)
+{
+    constexpr int RG = 2 * C * kWarps;
+    __shared__ GroupShared gs;
+    __shared__ __align__(16) uint32_t bt_bufs[3 * kChunk * RG];   // warp 0's walk
+    const int W = a.W, Wg = W / kWarps, Lg = Wg / C, half = W / 2;
+    ReadCtx r;
+    r.ev = a.events + d.ev_off;
+    r.kc = a.kc + d.kc_off;
+    r.tr = a.trace + d.tr_off;
+    r.mv = a.moves + d.mv_off;
+    r.n_e = d.n_e;
+    r.n_k = d.n_k;
+    r.W = W;
+    r.L = Lg;
+    r.Wp = Wg;
+    r.lane = lane;
+    r.src_up = (lane + 31) & 31;
+    r.first_lane = lane == 0;
+    r.last_lane = lane == Lg - 1;
+    r.lane31 = lane == 31;
+    r.dead_mask = 0;
+#pragma unroll
+    for (int i = 0; i < C; i++)
+        if (C * lane + i >= Wg) r.dead_mask |= 1u << i;
+    r.cs = Consts{d.lp_skip, d.lp_stay, d.lp_step, d.lp_trim};
+    const bool live = lane < Lg;
+    r.lsk = live ? d.lp_skip : neg_inf();
+    r.off0 = warp * Wg;
+    r.gw = warp;
+    r.xch = &gs.xch[0][0];
+    r.rx = gs.rx;
+
+    Lane<C> s;
+    float P[C], PP[C];
+    s.ll_e = half;
+    s.ll_k = -1 - half;
+#pragma unroll
+    for (int i = 0; i < C; i++) {
+        const int j = r.off0 + C * lane + i;
+        PP[i] = (live && j == half) ? 0.0f : neg_inf();
+        P[i] = (live && j == half) ? d.lp_trim : neg_inf();
+        s.X[i] = event_value(r.ev, s.ll_e - j, r.n_e);
+        const float4 q = live ? kmer_operands(r.kc, s.ll_k + j, r.n_k) : no_kmer();
+        s.A[i] = q.x;
+        s.B[i] = q.y;
+        s.Cc[i] = q.z;
+    }
+    // band 1's shifted view of band 0 (S_0 one offset below the lane's first slot)
+    s.qprev = (live && r.off0 + C * lane - 1 == half) ? 0.0f : neg_inf();
+    // the neighbour warps' edges of band 1 (its only finite cell is at offset W/2)
+    s.nb_lo = (warp > 0 && r.off0 - 1 == half) ? d.lp_trim : neg_inf();
+    s.nb_hi = (warp < kWarps - 1 && r.off0 + Wg == half) ? d.lp_trim : neg_inf();
+    s.kprev = false;
+    s.ev_base = s.ll_e + 1 - r.off0;
+    s.ev_cur = event_value(r.ev, s.ev_base + lane, r.n_e);
+    s.ev_nxt = event_value(r.ev, s.ev_base + 32 + lane, r.n_e);
+    s.kc_base = s.ll_k + r.off0 + Wg;
+    s.kc_cur = kmer_operands(r.kc, s.kc_base + lane, r.n_k);
+    s.kc_nxt = kmer_operands(r.kc, s.kc_base + 32 + lane, r.n_k);
+    next_event(s, r, s.ll_e + 1 - r.off0);
+    next_kmer(s, r, s.ll_k + r.off0 + Wg);
+    s.b = 1;
+    s.knext = general_move<C>(s, r, (half == 0) ? d.lp_trim : neg_inf(), (half == W - 1) ? d.lp_trim : neg_inf());
+    s.b = 2;
+    s.frame = 0.0;
+    s.best = -(double)pos_inf();
+    s.best_e = INT_MAX;
+    s.best_le = 0;
+    s.cells = 0;
+    s.lean_bands = 0;
+
+    band_loop<C, false, false, true>(s, r, P, PP);
+
+    double best = s.best;
+    int best_e = s.best_e, best_le = s.best_le;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(kFull, best, off);
+        const int oe = __shfl_xor_sync(kFull, best_e, off);
+        const int ol = __shfl_xor_sync(kFull, best_le, off);
+        if (ob > best || (ob == best && oe < best_e)) {
+            best = ob;
+            best_e = oe;
+            best_le = ol;
+        }
+    }
+    if (lane == 0) {
+        gs.best[warp] = best;
+        gs.best_e[warp] = best_e;
+        gs.best_le[warp] = best_le;
+    }
+    __threadfence();                      // this warp's trace records, before warp 0 reads them
+    group_sync();
+    if (warp != 0) return;
+#pragma unroll
+    for (int g = 1; g < kWarps; g++) {
+        const double ob = gs.best[g];
+        const int oe = gs.best_e[g];
+        if (ob > best || (ob == best && oe < best_e)) {
+            best = ob;
+            best_e = oe;
+            best_le = gs.best_le[g];
+        }
+    }
+    const long long cells = s.cells + s.lean_bands * (long long)W;
+
+    int status = ABEA_READ_OK;
+    int n = 0;
+    int2 *out = reinterpret_cast<int2 *>(a.pairs) + d.pair_off;
+    const int cap = d.pair_cap;
+    if (best == -(double)pos_inf()) {
+        status = ABEA_READ_FAIL_NO_END;
+    } else {
+        const unsigned magic = 0xffffffffu / (unsigned)Wg + 1u;
+        const int rc = backtrack<C, RG, false, true>(r, bt_bufs, best_e, best_le, out, cap, n, (unsigned)Wg, magic);
+        if (rc != 0) {
+            status = ABEA_READ_FAIL_NO_END;
+            n = 0;
+        } else if (n > cap) {
+            status = ABEA_READ_CAPACITY;
+        } else {
+            compact_pairs(out, cap, n, lane);
+        }
+    }
+    if (lane == 0) {
+        abea_result res;
+        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY) ? __double2float_rn(best) : neg_inf();
+        res.status = status;
+        res.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
+        res.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : best_e;
+        res.cells = cells;
+        a.res[rid] = res;
+    }
+}
+
+// Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
+// n_group-1] in block mode (CG offsets per lane); then every warp takes reads
+// order[n_group ..] one at a time from the shared counter.
+template <int C, bool MIXED, bool FULLW, int CG>
 __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(const AlignArgs a)
 {
     constexpr int R = Rec<C>::R;
     __shared__ __align__(16) uint32_t bt[kWarps][3 * kChunk * R];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    if (CG > 0 && (int)blockIdx.x < a.n_group) {
+        const int rid = a.order[blockIdx.x];
+        const ReadDesc d = a.rd[rid];
+        if (d.host_bad || a.flags[rid]) {
+            if (threadIdx.x == 0) {
+                abea_result res;
+                res.score = neg_inf();
+                res.status = ABEA_READ_BAD_INPUT;
+                res.n_pairs = 0;
+                res.e_end = -1;
+                res.cells = 0;
+                a.res[rid] = res;
+            }
+        } else {
+            align_read_group<(CG > 0 ? CG : 1)>(a, d, rid, warp, lane);
+        }
+        __syncwarp();
+    }
     for (;;) {
         int q = 0;
         if (lane == 0) q = atomicAdd(a.queue, 1);
-        q = __shfl_sync(kFull, q, 0);
+        q = __shfl_sync(kFull, q, 0) + a.n_group;
         if (q >= a.n) break;
         const int rid = a.order[q];
         const ReadDesc d = a.rd[rid];
@@ -829,22 +1110,35 @@ __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(co
     }
 }
 
-template <int C, bool MIXED, bool FULLW>
+template <int C, bool MIXED, bool FULLW, int CG>
 int launch_c(const AlignArgs &a, int grid, void *stream)
 {
-    align_kernel<C, MIXED, FULLW><<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
+    align_kernel<C, MIXED, FULLW, CG><<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 
-template <int C, bool MIXED, bool FULLW>
+template <int C, bool MIXED, bool FULLW, int CG>
 int grid_c(int device)
 {
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return -1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_kernel<C, MIXED, FULLW>, kWarps * 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_kernel<C, MIXED, FULLW, CG>, kWarps * 32, 0);
     if (e != cudaSuccess || per_sm < 1) return -1;
     return sms * per_sm;
+}
+
+// Offsets per lane in block mode for band width W (0: no block mode): W
+// splits evenly over the block's warps, W' = W / kWarps, and W' = c * L'
+// with L' <= 31 lanes (lane 31 stays above the band and carries the move
+// bit), c = 1 or 2.  Narrow bands (W < 32) gain nothing from it.
+int group_offsets_per_lane(int W)
+{
+    if (W < 32 || W % kWarps != 0) return 0;
+    const int Wg = W / kWarps;
+    for (int c = 1; c <= 2; c++)
+        if (Wg % c == 0 && Wg / c <= 31) return c;
+    return 0;
 }
 
 }  // namespace
@@ -865,33 +1159,63 @@ Geometry geometry_for(int W)
     g.Wp = C * g.L;
     g.mixed = g.Wp != W;
     g.full = g.L == 32;
-    g.rec_words = (2 * C + 3) / 4 * 4;
+    g.cg = group_offsets_per_lane(W);
+    g.rec_words = std::max((2 * C + 3) / 4 * 4, 2 * g.cg * kWarps);
     return g;
 }
 
-#define ABEA_FOR_EACH_C(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
-
-int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream)
+int group_count(const ReadDesc *rd, const int32_t *order, int32_t n, const Geometry &g, int grid, double theta)
 {
-#define X(c)                                                                                      \
-    if (g.C == c) {                                                                               \
-        if (g.mixed)                                                                              \
-            return g.full ? launch_c<c, true, true>(a, grid, stream) : launch_c<c, true, false>(a, grid, stream); \
-        return g.full ? launch_c<c, false, true>(a, grid, stream) : launch_c<c, false, false>(a, grid, stream);   \
+    if (g.cg == 0 || n <= 0 || grid <= 0 || !(theta > 0.0)) return 0;
+    double total = 0.0;
+    for (int32_t t = 0; t < n; t++)
+        if (!rd[t].host_bad) total += (double)rd[t].n_e + rd[t].n_k + 1;
+    const double slots = (double)std::min<int64_t>((int64_t)grid, (n + kWarps - 1) / kWarps) * kWarps;
+    const double limit = theta * total / slots;
+    int m = 0;
+    while (m < n && m < grid) {
+        const ReadDesc &d = rd[order[m]];
+        if (d.host_bad || (double)d.n_e + d.n_k + 1 <= limit) break;
+        m++;
     }
-    ABEA_FOR_EACH_C(X)
+    return m;
+}
+
+int align_launch_grid(int32_t n, int n_group, int grid)
+{
+    const int64_t want = (int64_t)n_group + (n - n_group + kWarps - 1) / kWarps;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(grid, want));
+}
+
+// Instantiated geometries: every (C, mixed, full, block-mode C) that
+// geometry_for gives for 2 <= W <= 256.
+#define ABEA_FOR_EACH_GEOMETRY(X)                                                                  \
+    X(1, false, false, 0) X(1, false, true, 1) X(2, false, false, 0) X(2, false, false, 1)         \
+    X(2, false, true, 1) X(2, true, false, 0) X(3, false, false, 0) X(3, false, false, 1)          \
+    X(3, false, true, 1) X(3, true, false, 0) X(3, true, true, 0) X(4, false, false, 1)            \
+    X(4, false, true, 2) X(4, true, false, 0) X(4, true, true, 0) X(5, false, false, 0)            \
+    X(5, false, true, 2) X(5, true, false, 0) X(5, true, true, 0) X(6, false, false, 0)            \
+    X(6, false, false, 2) X(6, false, true, 2) X(6, true, false, 0) X(6, true, true, 0)            \
+    X(7, false, false, 0) X(7, false, true, 2) X(7, true, false, 0) X(7, true, true, 0)            \
+    X(8, false, false, 2) X(8, false, true, 0) X(8, true, false, 0) X(8, true, true, 0)
+
+int launch_align(const AlignArgs &args, const Geometry &g, int grid, void *stream)
+{
+    AlignArgs a = args;
+    a.n_group = std::max(0, std::min(std::min(a.n_group, a.n), grid));
+    if (g.cg == 0) a.n_group = 0;
+#define X(c_, m_, f_, g_)                                                                          \
+    if (g.C == c_ && g.mixed == m_ && g.full == f_ && g.cg == g_) return launch_c<c_, m_, f_, g_>(a, grid, stream);
+    ABEA_FOR_EACH_GEOMETRY(X)
 #undef X
     return (int)cudaErrorInvalidValue;
 }
 
 int align_grid_size(const Geometry &g, int device)
 {
-#define X(c)                                                                                      \
-    if (g.C == c) {                                                                               \
-        if (g.mixed) return g.full ? grid_c<c, true, true>(device) : grid_c<c, true, false>(device); \
-        return g.full ? grid_c<c, false, true>(device) : grid_c<c, false, false>(device);         \
-    }
-    ABEA_FOR_EACH_C(X)
+#define X(c_, m_, f_, g_)                                                                          \
+    if (g.C == c_ && g.mixed == m_ && g.full == f_ && g.cg == g_) return grid_c<c_, m_, f_, g_>(device);
+    ABEA_FOR_EACH_GEOMETRY(X)
 #undef X
     return -1;
 }

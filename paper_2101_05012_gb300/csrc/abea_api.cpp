@@ -59,7 +59,8 @@ struct abea_ctx {
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
     int32_t last_launches = 0;                  // kernel launches since the last stats call
-    int grid[9][2][2] = {};
+    int grid[9][2][2][3] = {};
+    double block_theta = abea::kDefaultBlockTheta;   // block mode for reads above theta x the even share
 };
 
 namespace {
@@ -235,9 +236,10 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
                                                        (int32_t *)c->flags.p, st))))
         return rc;
     c->last_launches++;
-    int &grid = c->grid[g.C][g.mixed ? 1 : 0][g.full ? 1 : 0];
+    int &grid = c->grid[g.C][g.mixed ? 1 : 0][g.full ? 1 : 0][g.cg];
     if (grid <= 0) grid = abea::align_grid_size(g, c->device);
     if (grid <= 0) return ABEA_ERR_CUDA;
+    const int n_group = abea::group_count(h_rd, h_order, n, g, grid, c->block_theta);
     AlignArgs a;
     a.rd = (const ReadDesc *)c->rd.p;
     a.order = (const int32_t *)c->order.p;
@@ -253,6 +255,7 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
     a.pairs = d_pairs;
     a.res = d_res;
     a.queue = (int32_t *)c->queue.p;
+    a.n_group = n_group;
     const int wave = std::min<int>(c->n_timed, kMaxTimed - 1);   // past the cap the last slot is reused
     while ((int)c->wave_t0.size() <= wave) {
         cudaEvent_t e0, e1;
@@ -261,7 +264,7 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
         c->wave_t1.push_back(e1);
     }
     if ((rc = cuda_err(cudaEventRecord(c->wave_t0[wave], st)))) return rc;
-    const int launch_grid = std::min<int>(grid, std::max<int>(1, (n + 3) / 4));
+    const int launch_grid = abea::align_launch_grid(n, n_group, grid);
     if ((rc = cuda_err((cudaError_t)abea::launch_align(a, g, launch_grid, st)))) return rc;
     c->last_launches++;
     if ((rc = cuda_err(cudaEventRecord(c->wave_t1[wave], st)))) return rc;
@@ -622,6 +625,13 @@ int abea_align(abea_ctx *c, const abea_read *read, int W, abea_result *out, int3
     int rc = abea_align_batch(c, read, 1, W, out, pairs, po, nullptr);
     if (rc) return rc;
     if (out->status == ABEA_READ_CAPACITY) return ABEA_ERR_CAPACITY;
+    return ABEA_OK;
+}
+
+int abea_set_block_mode(abea_ctx *c, double theta)
+{
+    if (!c || std::isnan(theta)) return ABEA_ERR_ARG;
+    c->block_theta = theta;
     return ABEA_OK;
 }
 

@@ -38,9 +38,11 @@ struct ModelRow {
 
 // Band-record geometry for a band width W: C offsets per lane, L lanes,
 // W' = C*L >= W physical offsets (mixed: W' > W), full: L == 32 (no lane
-// above the band), rec_words uint32 words of trace per band.
+// above the band); cg offsets per lane when a block's warps share one read
+// (0: never); rec_words uint32 words of trace reserved per band (the larger
+// record of the two modes).
 struct Geometry {
-    int C, L, Wp, rec_words;
+    int C, L, Wp, rec_words, cg;
     bool mixed, full;
 };
 Geometry geometry_for(int W);
@@ -60,6 +62,7 @@ struct AlignArgs {
     int32_t *pairs;            // int32 pairs, (event, k-mer)
     abea_result *res;
     int32_t *queue;            // work counter, zeroed before the launch
+    int32_t n_group;           // order[0 .. n_group-1] run in block mode (one read per block)
 };
 
 // Launchers (return cudaError_t as int).
@@ -67,5 +70,14 @@ int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *
                 const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
 int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream);
 int align_grid_size(const Geometry &g, int device);
+
+constexpr double kDefaultBlockTheta = 1.0;
+
+// How many of the longest reads (order[0..], longest first) run in block
+// mode: those with more than theta times the bands each warp of the launch
+// would get if the batch were spread evenly, at most one per block.
+int group_count(const ReadDesc *rd, const int32_t *order, int32_t n, const Geometry &g, int grid, double theta);
+// Blocks to launch for n reads of which n_group run in block mode (at most grid).
+int align_launch_grid(int32_t n, int n_group, int grid);
 
 }  // namespace abea

@@ -50,7 +50,7 @@ ReadDesc s_desc[kMaxReads];
 int32_t s_order[kMaxReads];
 int64_t s_key[kMaxReads];
 unsigned char *s_scratch[kMaxDevices];               // device address of g_scratch, per device
-int s_grid[kMaxDevices][9][2][2];
+int s_grid[kMaxDevices][9][2][2][3];
 std::mutex s_setup;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -187,9 +187,10 @@ extern "C" int abea_align_batch_device_noalloc(int k, const float *level_mean, c
                                (const ModelRow *)(base + off_rows), k, (float4 *)(base + off_kc),
                                (int32_t *)(base + off_flags), st);
     if (rc != cudaSuccess) return ABEA_ERR_CUDA;
-    int &grid = s_grid[device][g.C][g.mixed ? 1 : 0][g.full ? 1 : 0];
+    int &grid = s_grid[device][g.C][g.mixed ? 1 : 0][g.full ? 1 : 0][g.cg];
     if (grid <= 0) grid = abea::align_grid_size(g, device);
     if (grid <= 0) return ABEA_ERR_CUDA;
+    const int n_group = abea::group_count(s_desc, s_order, n, g, grid, abea::kDefaultBlockTheta);
     AlignArgs a;
     a.rd = (const ReadDesc *)(base + off_desc);
     a.order = (const int32_t *)(base + off_order);
@@ -205,6 +206,7 @@ extern "C" int abea_align_batch_device_noalloc(int k, const float *level_mean, c
     a.pairs = d_pairs;
     a.res = d_out;
     a.queue = (int32_t *)(base + off_queue);
-    rc = abea::launch_align(a, g, std::min<int>(grid, std::max<int>(1, (n + 3) / 4)), st);
+    a.n_group = n_group;
+    rc = abea::launch_align(a, g, abea::align_launch_grid(n, n_group, grid), st);
     return rc == cudaSuccess ? ABEA_OK : ABEA_ERR_CUDA;
 }

@@ -25,9 +25,17 @@ def ctx():
     c.close()
 
 
-def run_gpu(ctx, batch, W=None, **kw):
+# block mode for every read a block can take (one per block, longest first)
+ALL_BLOCK = 1e-9
+
+
+def run_gpu(ctx, batch, W=None, theta=1.0, **kw):
     ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
-    return ctx.align_packed(batch, W=W, **kw)
+    ctx.set_block_mode(theta)
+    try:
+        return ctx.align_packed(batch, W=W, **kw)
+    finally:
+        ctx.set_block_mode(1.0)
 
 
 def gpu_pairs(pairs, pair_off, res, i):
@@ -97,6 +105,33 @@ def test_band_widths(ctx, W):
     compare(b, res, pairs, po, W=W)
 
 
+# one width per (lanes, offsets per lane) combination that block mode has
+@pytest.mark.parametrize("W", [32, 36, 64, 72, 96, 100, 128, 144, 160, 192, 200, 224, 248])
+def test_block_mode_band_widths(ctx, W):
+    """Block mode (the four warps of a block share a read) on every read,
+    and per-warp mode only, both against the oracle."""
+    lengths = [6, 9, 30, 80, 150, 260, 420, 700, 1500]
+    b = _lengths_batch(lengths, W=W, seed=300 + W)
+    res, pairs, po = run_gpu(ctx, b, W=W, theta=ALL_BLOCK)
+    compare(b, res, pairs, po, W=W, check_f64=False)
+    res0, pairs0, po0 = run_gpu(ctx, b, W=W, theta=0.0)
+    assert np.array_equal(res, res0)
+    assert np.array_equal(pairs, pairs0)
+
+
+def test_block_mode_long_reads(ctx):
+    """Long reads in block mode (renormalisation, walks across many trace
+    chunks) next to short ones in the same launch."""
+    w = synth.WORKLOADS["batch_4096_ln5kb"]
+    L = synth.read_lengths(w)
+    ids = sorted(set(np.argsort(-L)[:2].tolist()) | {0, 1, 2, 3})     # two 50 kb reads and four others
+    b = synth.make_batch(w, read_ids=ids)
+    for theta in (ALL_BLOCK, 1.0, 0.0):
+        res, pairs, po = run_gpu(ctx, b, theta=theta)
+        assert np.all(res["status"] == 0)
+        compare(b, res, pairs, po, check_f64=False)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 7, 9])
 def test_kmer_sizes(ctx, k):
     lengths = [k, k + 1, 40, 300, 900]
@@ -105,7 +140,8 @@ def test_kmer_sizes(ctx, k):
     compare(b, res, pairs, po)
 
 
-def test_bad_inputs_and_neighbours(ctx):
+@pytest.mark.parametrize("theta", [1.0, ALL_BLOCK])
+def test_bad_inputs_and_neighbours(ctx, theta):
     good = _lengths_batch([300, 500, 700], seed=3)
     ev, sq, sc = [], [], []
     for i in range(good.n):
@@ -125,14 +161,15 @@ def test_bad_inputs_and_neighbours(ctx):
     all_sq = [sq[1]] + [c[1] for c in cases] + [sq[2]]
     all_sc = [sc[1]] + [c[2] for c in cases] + [sc[2]]
     b = synth.custom_batch(all_ev, all_sq, all_sc, good.model_mean, good.model_stdv, good.k, good.W)
-    res, pairs, po = run_gpu(ctx, b)
+    res, pairs, po = run_gpu(ctx, b, theta=theta)
     assert res["status"][0] == 0 and res["status"][-1] == 0
     assert np.all(res["status"][1:-1] == binding.READ_BAD_INPUT), res["status"]
     assert np.all(np.isneginf(res["score"][1:-1]))
     compare(b, res, pairs, po, ids=[0, b.n - 1])
 
 
-def test_capacity(ctx):
+@pytest.mark.parametrize("theta", [1.0, ALL_BLOCK])
+def test_capacity(ctx, theta):
     b = _lengths_batch([200, 400, 600], seed=8)
     o = oracle.abea_batch(b, "f32", n_threads=THREADS)
     need = o["n_pairs"]
@@ -140,7 +177,7 @@ def test_capacity(ctx):
     caps[1] = need[1] - 1                        # one pair short
     po = np.zeros(b.n + 1, np.int64)
     np.cumsum(caps, out=po[1:])
-    res, pairs, po = run_gpu(ctx, b, pair_off=po)
+    res, pairs, po = run_gpu(ctx, b, pair_off=po, theta=theta)
     assert res["status"][1] == binding.READ_CAPACITY and res["n_pairs"][1] == need[1]
     assert res["status"][0] == 0 and res["status"][2] == 0
     for i in (0, 2):
@@ -173,8 +210,8 @@ def test_extreme_events(ctx):
         sqs.append(s)
         scs.append(c)
     b = synth.custom_batch(evs, sqs, scs, base.model_mean, base.model_stdv, base.k, base.W)
-    for W in (3, 100):
-        res, pairs, po = run_gpu(ctx, b, W=W)
+    for W, theta in ((3, 1.0), (100, 1.0), (100, ALL_BLOCK)):
+        res, pairs, po = run_gpu(ctx, b, W=W, theta=theta)
         compare(b, res, pairs, po, W=W, check_f64=False)
 
 
