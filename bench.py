@@ -16,6 +16,11 @@ as reads/s.
           buffers, one host thread per context; each step copies its inputs
           host->device and its results device->host inside the timed region.
 
+serving: serve_mix requests (70 % 400-base prefixes, 30 % full reads) with
+seeded Poisson arrivals at 1x and 10x the offered load of 512 channels x 450
+bases/s, through abea_server_*; p50/p99 from submission to the result in
+host memory, per class.
+
 --impl reference runs the CPU oracle (oracle/, FP32) on bounded samples of
 the same workload.  With --gpus N > 1 each rank runs its own replica of the
 workload (reads are independent; there is no data exchange).
@@ -56,6 +61,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--depth", type=int, default=3, help="batches in flight (one context and stream each)")
+    p.add_argument("--serve-requests", type=int, default=500,
+                   help="serve_mix requests at 1x offered load (4x as many at 10x); 0 skips serving")
     p.add_argument("--block-theta", type=float, default=0.0,
                    help="reads above this multiple of the even per-warp share of bands run on a whole block "
                         "(<= 0: one warp per read)")
@@ -151,6 +158,56 @@ def oracle_rate(batch, seconds: float, threads: int):
     dt = time.perf_counter() - t
     return (float(r["cells"].sum()) / dt / 1e9, m / dt,
             f"{m} of {n} reads, evenly spaced ({int(r['cells'].sum())} cells), {dt:.1f} s wall")
+
+
+def serve_latency(binding, synth, device: int, load: float, n_req: int, theta: float):
+    """serve_mix through the serving loop: seeded Poisson arrivals at `load` x the offered load of
+    512 channels x 450 bases/s; latency from submission to the result in host memory, as the
+    server stamps it."""
+    import threading
+    batch, arrival, is_prefix = synth.serving_requests(n_req, load=load)
+    ctx = binding.Context(device)
+    ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
+    srv = binding.Server(ctx, batch.W, max_batch_reads=256, max_wait_us=200, batches_in_flight=3,
+                         block_theta=theta)
+    reads = [batch.read(i) for i in range(batch.n)]
+    warm = [srv.submit(*reads[i]) for i in range(min(32, batch.n))]
+    for t in warm:
+        while srv.poll(t, wait_us=100_000) is None:
+            pass
+    tickets = [None] * batch.n
+    lat = np.zeros(batch.n)
+    ready = threading.Semaphore(0)
+
+    def poller():
+        for i in range(batch.n):
+            ready.acquire()
+            while True:
+                r = srv.poll(tickets[i], wait_us=100_000)
+                if r is not None:
+                    lat[i] = r[2]
+                    break
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(batch.n):
+        d = t0 + arrival[i] - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets[i] = srv.submit(*reads[i])
+        ready.release()
+    th.join()
+    wall = time.perf_counter() - t0
+    srv.stop()
+    ctx.close()
+    ms = lat / 1e3
+    pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
+    cls = {"prefix_400b": ms[is_prefix], "full_read": ms[~is_prefix]}
+    return {"load": load, "requests": int(batch.n), "offered_req_per_s": float(batch.n / arrival[-1]),
+            "served_req_per_s": float(batch.n / wall), "p50_ms": pct(ms, 50), "p99_ms": pct(ms, 99),
+            **{f"{k}_p50_ms": pct(v, 50) for k, v in cls.items()},
+            **{f"{k}_p99_ms": pct(v, 99) for k, v in cls.items()}}
 
 
 def run_reference(args):
@@ -358,6 +415,11 @@ def run_ours(args):
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = [serve_latency(binding, synth, local_rank, load, n_req, 1.0)
+                   for load, n_req in ((1.0, args.serve_requests), (10.0, 4 * args.serve_requests))]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads_n = os.cpu_count() or 1
@@ -379,7 +441,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
                         "host_threads": D},
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

@@ -160,6 +160,59 @@ int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kern
  * a NaN theta. */
 int abea_set_block_mode(abea_ctx *ctx, double theta);
 
+/* Serving loop (the paper has no counterpart: it aligns files batch by
+ * batch).  Requests (one read each) are admitted one at a time and aligned
+ * in micro-batches while earlier ones are still running:
+ *
+ *   abea_server_start(ctx, &cfg, &srv);
+ *   abea_server_submit(srv, &read, &ticket);          (any host thread)
+ *   abea_server_poll(srv, ticket, wait_us, &res, pairs, cap, &latency_us);
+ *   abea_server_stop(srv);
+ *
+ * A worker thread closes a micro-batch when it holds max_batch_reads
+ * requests or max_wait_us after its first request arrived, whichever comes
+ * first, and runs it on one of batches_in_flight internal contexts (each
+ * with its own stream and page-locked staging) on ctx's device, with ctx's
+ * model; each internal context gets 1/batches_in_flight of ctx's memory
+ * budget, and a micro-batch stays within it.  Results equal those of
+ * abea_align for the same read (the kernels do not depend on the batch).
+ * ctx must stay alive (and its model unchanged) until abea_server_stop. */
+typedef struct abea_server abea_server;
+typedef struct {
+    int W;                     /* band width of every request (2..256) */
+    int32_t max_batch_reads;   /* 0: 256 */
+    int32_t max_wait_us;       /* 0: 200; a micro-batch waits at most this long for more requests */
+    int32_t batches_in_flight; /* 0: 3 */
+    int32_t max_requests;      /* 0: 65536; requests submitted and not yet polled to completion */
+    double block_theta;        /* per micro-batch, as abea_set_block_mode (<= 0: off) */
+} abea_server_cfg;
+
+/* Returns ABEA_ERR_NO_MODEL if ctx has no model, ABEA_ERR_ARG for a bad cfg. */
+int abea_server_start(abea_ctx *ctx, const abea_server_cfg *cfg, abea_server **out);
+
+/* Copies the read (events, bases, scalings) and queues it; *ticket names it
+ * for abea_server_poll.  ABEA_ERR_CAPACITY: max_requests are outstanding
+ * (poll some, then retry).  ABEA_ERR_NOMEM: the read alone exceeds an
+ * internal context's memory budget.  ABEA_ERR_ARG: bad read or the server
+ * is stopping.  Thread-safe. */
+int abea_server_submit(abea_server *srv, const abea_read *read, int64_t *ticket);
+
+/* Waits up to wait_us microseconds (0: no wait) for the request to finish.
+ * ABEA_OK: *out holds its result, its pairs (out->n_pairs of them, event
+ * and k-mer index, ascending) are in pairs[0 .. 2*n_pairs), *latency_us (if
+ * not NULL) is the time from submission to the result being in host
+ * memory, and the ticket is retired.  ABEA_ERR_TIMEOUT: not finished yet.
+ * ABEA_ERR_CAPACITY: finished but cap < out->n_pairs; *out is filled and
+ * the ticket stays valid for another poll.  ABEA_ERR_ARG: unknown or
+ * retired ticket.  ABEA_ERR_CUDA: its micro-batch failed on the device.
+ * Thread-safe; one poller per ticket. */
+int abea_server_poll(abea_server *srv, int64_t ticket, int32_t wait_us, abea_result *out, int32_t *pairs,
+                     int32_t cap, double *latency_us);
+
+/* Finishes the queued and running requests, stops the worker and frees
+ * everything (unpolled results are dropped). */
+int abea_server_stop(abea_server *srv);
+
 /* The paper has no counterpart to this call.  abea_align_batch_device without
  * any memory allocation, for callers that cannot call cudaMalloc: for
  * example a plugin inside a host application that already holds (nearly)

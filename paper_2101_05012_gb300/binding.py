@@ -28,7 +28,8 @@ READ_OK, READ_FAIL_NO_END, READ_BAD_INPUT, READ_CAPACITY = range(4)
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
-           "abea_set_block_mode", "abea_align_batch_device_noalloc"]
+           "abea_set_block_mode", "abea_server_start", "abea_server_submit", "abea_server_poll",
+           "abea_server_stop", "abea_align_batch_device_noalloc"]
 
 
 class Scalings(ctypes.Structure):
@@ -38,6 +39,12 @@ class Scalings(ctypes.Structure):
 class Read(ctypes.Structure):
     _fields_ = [("ev_mean", ctypes.c_void_p), ("n_events", ctypes.c_int32), ("seq", ctypes.c_void_p),
                 ("seq_len", ctypes.c_int32), ("sc", Scalings)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("max_batch_reads", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
+                ("batches_in_flight", ctypes.c_int32), ("max_requests", ctypes.c_int32),
+                ("block_theta", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -83,6 +90,10 @@ def load(path: Optional[str] = None):
     lib.abea_align_batch_device.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.abea_set_block_mode.argtypes = [P, ctypes.c_double]
+    lib.abea_server_start.argtypes = [P, ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
+    lib.abea_server_submit.argtypes = [P, ctypes.POINTER(Read), ctypes.POINTER(i64)]
+    lib.abea_server_poll.argtypes = [P, i64, i32, ctypes.POINTER(Result), P, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.abea_server_stop.argtypes = [P]
     lib.abea_align_batch_device_noalloc.argtypes = [ctypes.c_int, P, P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     for f in EXPORTS:
         if f not in ("abea_destroy", "abea_strerror"):
@@ -208,6 +219,60 @@ class Context:
         ms = ctypes.c_float()
         _check(self.lib.abea_last_launch_stats(self.h, ctypes.byref(n), ctypes.byref(ms)), "abea_last_launch_stats")
         return n.value, ms.value
+
+
+class Server:
+    """abea_server_*: continuous admission of single-read requests on a Context's device and model."""
+
+    def __init__(self, ctx: Context, W: int, max_batch_reads: int = 0, max_wait_us: int = 0,
+                 batches_in_flight: int = 0, max_requests: int = 0, block_theta: float = 1.0):
+        self.lib = ctx.lib
+        self.k = ctx.k
+        cfg = ServerCfg(W, max_batch_reads, max_wait_us, batches_in_flight, max_requests, float(block_theta))
+        h = ctypes.c_void_p()
+        _check(self.lib.abea_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h)), "abea_server_start")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, events, seq, scalings) -> int:
+        """Queue one read; returns its ticket.  Raises AbeaError (ABEA_ERR_CAPACITY when full)."""
+        ev = np.ascontiguousarray(events, np.float32)
+        sq = np.frombuffer(seq.encode() if isinstance(seq, str) else bytes(seq), np.uint8).copy()
+        rd = Read(_p(ev).value if len(ev) else None, len(ev), _p(sq).value if len(sq) else None, len(sq),
+                  Scalings(*[float(v) for v in scalings]))
+        t = ctypes.c_int64()
+        _check(self.lib.abea_server_submit(self.h, ctypes.byref(rd), ctypes.byref(t)), "abea_server_submit")
+        self._keep[t.value] = len(ev) + max(len(sq), 1)
+        return t.value
+
+    def poll(self, ticket: int, wait_us: int = 0):
+        """(result dict, pairs int32[n,2], latency_us), or None while the request runs."""
+        cap = max(self._keep.get(ticket, 1), 1)
+        pairs = np.zeros((cap, 2), np.int32)
+        res = Result()
+        lat = ctypes.c_double()
+        rc = self.lib.abea_server_poll(self.h, ticket, wait_us, ctypes.byref(res), _p(pairs), cap,
+                                       ctypes.byref(lat))
+        if rc == ABEA_ERR_TIMEOUT:
+            return None
+        _check(rc, "abea_server_poll")
+        self._keep.pop(ticket, None)
+        out = {f: getattr(res, f) for f, _ in Result._fields_}
+        return out, pairs[:res.n_pairs].copy() if res.status == READ_OK else pairs[:0], lat.value
+
+    def stop(self):
+        if getattr(self, "h", None):
+            self.lib.abea_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.stop()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
 
 
 def align_batch_device_noalloc(k: int, level_mean, level_stdv, n: int, W: int, d_seq, seq_off, d_events, ev_off,

@@ -1,6 +1,6 @@
 """Build libabea.so in-tree (paper_2101_05012_gb300/_build/) with nvcc for sm_103a.
 
-The three translation units compile in parallel; the CUDA runtime is linked
+The translation units compile in parallel; the CUDA runtime is linked
 statically so the library needs only the driver at run time.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libabea.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["abea_align.cu", "abea_prep.cu", "abea_api.cpp", "abea_noalloc.cu"]
+SOURCES = ["abea_align.cu", "abea_prep.cu", "abea_api.cpp", "abea_noalloc.cu", "abea_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

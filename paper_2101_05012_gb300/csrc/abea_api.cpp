@@ -59,6 +59,7 @@ struct abea_ctx {
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
     int32_t last_launches = 0;                  // kernel launches since the last stats call
+    std::vector<float> h_mean, h_stdv;          // the model as set (host copy)
     int grid[9][2][2][3] = {};
     double block_theta = abea::kDefaultBlockTheta;   // block mode for reads above theta x the even share
 };
@@ -300,7 +301,7 @@ bool is_page_locked(const void *p)
 // to the caller's arrays (no staging copy on the host).
 int packed_direct(abea_ctx *c, const Geometry &g, int32_t n, int W, const char *seq, const int64_t *seq_off,
                   const float *events, const int64_t *ev_off, const abea_scalings *sc, abea_result *out,
-                  int32_t *pairs, const int64_t *pair_off, cudaStream_t st)
+                  int32_t *pairs, const int64_t *pair_off, cudaStream_t st, bool wait = true)
 {
     int rc;
     const int64_t ns = seq_off[n] - seq_off[0], ne = ev_off[n] - ev_off[0], np = pair_off[n] - pair_off[0];
@@ -334,8 +335,17 @@ int packed_direct(abea_ctx *c, const Geometry &g, int32_t n, int W, const char *
     if (np > 0 && (rc = cuda_err(cudaMemcpyAsync(pairs + 2 * pair_off[0], c->pairs.p, 8 * (size_t)np,
                                                  cudaMemcpyDeviceToHost, st))))
         return rc;
-    if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+    if (wait && (rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
     return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+// Device bytes one read needs in a wave (working set plus its inputs and outputs).
+size_t read_bytes(const abea_ctx *c, const Geometry &g, int64_t n_e, int64_t seq_len, int64_t pair_cap)
+{
+    const int64_t n_k = seq_len - c->k + 1;
+    const Footprint f = footprint(std::max<int64_t>(n_e, 0), std::max<int64_t>(n_k, 0), g);
+    return work_bytes(1, f) + (size_t)seq_len + 4 * (size_t)std::max<int64_t>(n_e, 0) + 8 * (size_t)pair_cap +
+           sizeof(abea_result);
 }
 
 }  // namespace
@@ -437,6 +447,8 @@ int abea_set_model(abea_ctx *c, int k, const float *level_mean, const float *lev
     int rc = cuda_err(cudaMemcpy(c->model.p, m.data(), rows * sizeof(ModelRow), cudaMemcpyHostToDevice));
     if (rc) return rc;
     c->k = k;
+    c->h_mean.assign(level_mean, level_mean + rows);
+    c->h_stdv.assign(level_stdv, level_stdv + rows);
     return ABEA_OK;
 }
 
@@ -503,12 +515,8 @@ int abea_align_packed(abea_ctx *c, int32_t n, int W, const char *seq, const int6
         std::vector<int32_t> cur;
         size_t cur_bytes = 0;
         for (int32_t i : all) {
-            const int64_t n_e = ev_off[i + 1] - ev_off[i];
-            const int64_t n_k = (seq_off[i + 1] - seq_off[i]) - c->k + 1;
-            const Footprint f = footprint(std::max<int64_t>(n_e, 0), std::max<int64_t>(n_k, 0), g);
-            const size_t io = (size_t)(seq_off[i + 1] - seq_off[i]) + 4 * (size_t)n_e +
-                              8 * (size_t)(pair_off[i + 1] - pair_off[i]) + sizeof(abea_result);
-            const size_t bytes = work_bytes(1, f) + io;
+            const size_t bytes = read_bytes(c, g, ev_off[i + 1] - ev_off[i], seq_off[i + 1] - seq_off[i],
+                                            pair_off[i + 1] - pair_off[i]);
             if (bytes > c->budget) return ABEA_ERR_NOMEM;
             if (!cur.empty() && cur_bytes + bytes > c->budget) {
                 waves.push_back(cur);
@@ -659,3 +667,46 @@ int abea_last_launch_stats(abea_ctx *c, int32_t *n_launches, float *align_kernel
 }
 
 }  // extern "C"
+
+// Internal entry points of the serving loop (abea_internal.h).
+namespace abea {
+
+int context_model(const abea_ctx *c, int *k, const float **mean, const float **stdv)
+{
+    if (!c || c->k <= 0) return ABEA_ERR_NO_MODEL;
+    *k = c->k;
+    *mean = c->h_mean.data();
+    *stdv = c->h_stdv.data();
+    return ABEA_OK;
+}
+
+int context_device(const abea_ctx *c) { return c->device; }
+
+size_t context_budget(const abea_ctx *c) { return c->budget; }
+
+void *context_stream(const abea_ctx *c) { return (void *)c->own_stream; }
+
+size_t request_bytes(const abea_ctx *c, int W, int64_t n_e, int64_t seq_len, int64_t pair_cap)
+{
+    return read_bytes(c, geometry_for(W), n_e, seq_len, pair_cap);
+}
+
+int align_packed_async(abea_ctx *c, int32_t n, int W, const char *seq, const int64_t *seq_off, const float *events,
+                       const int64_t *ev_off, const abea_scalings *sc, abea_result *out, int32_t *pairs,
+                       const int64_t *pair_off)
+{
+    int rc = check_common(c, W);
+    if (rc) return rc;
+    if (n <= 0 || !seq || !seq_off || !events || !ev_off || !sc || !out || !pair_off || !pairs) return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    const Geometry g = geometry_for(W);
+    size_t bytes = 0;
+    for (int32_t i = 0; i < n; i++)
+        bytes += read_bytes(c, g, ev_off[i + 1] - ev_off[i], seq_off[i + 1] - seq_off[i], pair_off[i + 1] - pair_off[i]);
+    if (bytes > c->budget) return ABEA_ERR_NOMEM;
+    cudaStream_t st = c->own_stream;
+    if ((rc = order_after_previous(c, st))) return rc;
+    return packed_direct(c, g, n, W, seq, seq_off, events, ev_off, sc, out, pairs, pair_off, st, false);
+}
+
+}  // namespace abea

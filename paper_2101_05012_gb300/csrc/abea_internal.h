@@ -80,4 +80,19 @@ int group_count(const ReadDesc *rd, const int32_t *order, int32_t n, const Geome
 // Blocks to launch for n reads of which n_group run in block mode (at most grid).
 int align_launch_grid(int32_t n, int n_group, int grid);
 
+// Context internals used by the serving loop.
+int context_model(const abea_ctx *c, int *k, const float **mean, const float **stdv);
+int context_device(const abea_ctx *c);
+size_t context_budget(const abea_ctx *c);
+void *context_stream(const abea_ctx *c);
+// Device bytes a read of n_e events and seq_len bases with pair_cap pairs needs in a batch.
+size_t request_bytes(const abea_ctx *c, int W, int64_t n_e, int64_t seq_len, int64_t pair_cap);
+// abea_align_packed for one wave whose host buffers are all page-locked (the
+// caller guarantees it), enqueued on the context's own stream without waiting;
+// ABEA_ERR_NOMEM if the batch exceeds the context's budget.  The buffers must
+// stay valid until the stream has passed the copies back.
+int align_packed_async(abea_ctx *c, int32_t n, int W, const char *seq, const int64_t *seq_off, const float *events,
+                       const int64_t *ev_off, const abea_scalings *sc, abea_result *out, int32_t *pairs,
+                       const int64_t *pair_off);
+
 }  // namespace abea
