@@ -74,6 +74,11 @@ constexpr int kWarps = 4;          // warps per block
 constexpr int kChunk = 32;         // bands per backtrack chunk
 constexpr int kRenormPeriod = 64;
 
+// Dynamic shared memory of the core kernel: the walk's record rings (one per
+// warp), then the block-mode exchange state.  Declared once so that every
+// function, including the out-of-line block mode, addresses it as shared.
+extern __shared__ __align__(16) uint32_t abea_smem[];
+
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 __device__ __forceinline__ float pos_inf() { return __int_as_float(0x7f800000); }
 
@@ -919,14 +924,16 @@ struct GroupShared {
 // per band.  Results equal those of the per-warp mode bit for bit (same
 // cells, same operations).
 // Out of line: inlined into the kernel, this code slows the per-warp loop by
-// about a fifth under full load (measured); its shared memory is its own, so
-// it is addressed as shared memory here.
+// about a fifth under full load (measured).  Its shared memory sits in the
+// kernel's dynamic shared memory: the exchange state at word gs_words, warp
+// 0's record ring (at least 3*kChunk*RG words) for the walk.
 template <int C>
-__device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc &d, int rid, int warp, int lane)
+__device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc &d, int rid, int warp, int lane,
+                                              int gs_words)
 {
     constexpr int RG = 2 * C * kWarps;
-    __shared__ GroupShared gs;
-    __shared__ __align__(16) uint32_t bt_bufs[3 * kChunk * RG];   // warp 0's walk
+    GroupShared &gs = *reinterpret_cast<GroupShared *>(abea_smem + gs_words);
+    uint32_t *bt_bufs = abea_smem;                                 // warp 0's ring serves the walk
     const int W = a.W, Wg = W / kWarps, Lg = Wg / C, half = W / 2;
     ReadCtx r;
     r.ev = a.events + d.ev_off;
@@ -1058,16 +1065,27 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
     }
 }
 
+// Dynamic shared memory layout for per-warp C and block-mode CG: per warp a
+// ring of 3*kChunk records of RB words (RB = the larger record of the two
+// modes), then the block-mode exchange state.
+template <int C, int CG>
+struct Smem {
+    static constexpr int RB = (CG > 0 && 2 * CG * kWarps > Rec<C>::R) ? 2 * CG * kWarps : Rec<C>::R;
+    static constexpr int GS_WORDS = kWarps * 3 * kChunk * RB;
+    static constexpr size_t BYTES =
+        4 * (size_t)GS_WORDS + (CG > 0 ? (sizeof(GroupShared) + 15) / 16 * 16 : 0);
+};
+
 // Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
 // n_group-1] in block mode (CG offsets per lane); then every warp takes reads
 // order[n_group ..] one at a time from the shared counter.
 template <int C, bool MIXED, bool FULLW, int CG>
 __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(const AlignArgs a)
 {
-    constexpr int R = Rec<C>::R;
-    __shared__ __align__(16) uint32_t bt[kWarps][3 * kChunk * R];
+    constexpr int RB = Smem<C, CG>::RB;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    uint32_t *bt = abea_smem + warp * 3 * kChunk * RB;
     if (CG > 0 && (int)blockIdx.x < a.n_group) {
         const int rid = a.order[blockIdx.x];
         const ReadDesc d = a.rd[rid];
@@ -1082,7 +1100,7 @@ __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(co
                 a.res[rid] = res;
             }
         } else {
-            align_read_group<(CG > 0 ? CG : 1)>(a, d, rid, warp, lane);
+            align_read_group<(CG > 0 ? CG : 1)>(a, d, rid, warp, lane, Smem<C, CG>::GS_WORDS);
         }
         __syncwarp();
     }
@@ -1105,7 +1123,7 @@ __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(co
             }
             continue;
         }
-        align_read<C, MIXED, FULLW>(a, d, rid, lane, bt[warp]);
+        align_read<C, MIXED, FULLW>(a, d, rid, lane, bt);
         __syncwarp();
     }
 }
@@ -1113,7 +1131,7 @@ __global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(co
 template <int C, bool MIXED, bool FULLW, int CG>
 int launch_c(const AlignArgs &a, int grid, void *stream)
 {
-    align_kernel<C, MIXED, FULLW, CG><<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(a);
+    align_kernel<C, MIXED, FULLW, CG><<<grid, kWarps * 32, Smem<C, CG>::BYTES, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 
@@ -1123,7 +1141,8 @@ int grid_c(int device)
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return -1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_kernel<C, MIXED, FULLW, CG>, kWarps * 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_kernel<C, MIXED, FULLW, CG>, kWarps * 32,
+                                                      Smem<C, CG>::BYTES);
     if (e != cudaSuccess || per_sm < 1) return -1;
     return sms * per_sm;
 }
