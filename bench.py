@@ -128,6 +128,43 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(x: float, world: int, dist=None, device=None) -> float:
+    """The largest of every rank's x (all ranks call it; one rank: x itself)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: int, steps: int, seconds: float, world: int) -> float:
+    """Whole-job rate: every rank processed its own copy of the workload (replicas), the job took
+    the slowest rank's time."""
+    return world * units_per_rank_step * steps / seconds
+
+
+def geometry(W: int):
+    """Offsets per lane C, whether lanes are partly filled, whether all 32 lanes are live, block-mode
+    offsets per lane (the same choice as the library's)."""
+    C = next((c for c in range((W + 31) // 32, 9) if W % c == 0), (W + 31) // 32)
+    L = -(-W // C)
+    cg = 0
+    if W >= 32 and W % 4 == 0:
+        cg = next((c for c in (1, 2) if (W // 4) % c == 0 and (W // 4) // c <= 31), 0)
+    return C, C * L != W, L == 32, cg
+
+
+def record_words(W: int) -> int:
+    C, _, _, cg = geometry(W)
+    return max((2 * C + 3) // 4 * 4, 8 * cg)
+
+
+def kernel_name(W: int) -> str:
+    C, mixed, full, cg = geometry(W)
+    return f"align_kernel<{C},{str(mixed).lower()},{str(full).lower()},{cg}>"
+
+
 def traffic_per_launch(bands: int):
     """DRAM bytes of one core-kernel launch over `bands` bands, from the ncu capture; None once the
     kernel source differs from the captured one."""
@@ -333,12 +370,10 @@ def run_ours(args):
         align_ms += ms
     if world > 1:
         dist.barrier()
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dist, dev)
     ms_step = ms_total / args.steps
-    value = world * cells * args.steps / (ms_total / 1e3) / 1e9
-    reads_per_s = world * n * args.steps / (ms_total / 1e3)
+    value = job_rate(cells, args.steps, ms_total / 1e3, world) / 1e9
+    reads_per_s = job_rate(n, args.steps, ms_total / 1e3, world)
 
     # end to end through the host-memory call (abea_align_packed, page-locked host buffers): one host
     # thread per context, each call copies its inputs in and its results out
@@ -383,14 +418,11 @@ def run_ours(args):
     if errors:
         raise binding.AbeaError(errors[0], "abea_align_packed")
     e2e_launches = sum(c.last_launch_stats()[0] for c in ctxs)
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s, world, dist, dev)
     for j in range(D):
         if not np.array_equal(binding.results_from_bytes(h_out[j]), res):
             raise SystemExit("bench: host-memory results differ from device-resident results")
-    e2e_value = world * cells * e2e_steps / e2e_s / 1e9
+    e2e_value = job_rate(cells, e2e_steps, e2e_s, world) / 1e9
     h2d = int(batch.seq.nbytes + batch.events.nbytes + n * (112 + 4))
     d2h = int(n * 24 + (pair_off[-1] - pair_off[0]) * 8)
 
@@ -406,9 +438,10 @@ def run_ours(args):
     achieved = cells * OPS_PER_CELL / (period_ms / 1e3) / 1e12
     peak = sms * 128 * sm_max * 1e6 / 1e12
     bands = int((batch.n_events() + batch.n_kmers() + 1).sum())
+    trace_bytes = bands * 4 * record_words(batch.W)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
                 "traffic": traffic_per_launch(bands),
-                "kernel": "align_kernel<4,false,false,1>", "launch_period_ms": period_ms,
+                "kernel": kernel_name(batch.W), "launch_period_ms": period_ms,
                 "launch_span_ms": span_ms, "batches_in_flight": D,
                 "ops_per_cell": OPS_PER_CELL,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)"}
@@ -435,7 +468,8 @@ def run_ours(args):
                            "events_per_step": int(batch.events.size),
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "batches_in_flight": D, "block_theta": args.block_theta,
-                           "l2": "inputs (195 MB events) and outputs (2.4 GB trace per step) exceed the 129 MB L2"},
+                           "l2": f"inputs ({batch.events.nbytes / 1e6:.0f} MB events) and the trace "
+                                 f"({trace_bytes / 1e9:.1f} GB per step) exceed the 129 MB L2"},
                 "reads_per_s": reads_per_s, "batch_latency_ms": statistics.median(lat),
                 "kernel_launch_span_ms": span_ms, "gpu_launches": launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
