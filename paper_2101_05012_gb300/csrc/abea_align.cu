@@ -697,12 +697,16 @@ __device__ __forceinline__ unsigned chunk_event_moves(const ReadCtx &r, int top,
 }
 
 // Walk the trace from (e_end, n_k-1) (whose band has offset-0 event le_end)
-// until an index leaves the matrix; lane 0 writes pair t of the walk to
-// out[cap-1-t] (t < cap).  Returns 0, or -1 if a traced cell lies outside
-// its band (cannot happen); n_out = pairs walked.  The records of 96 bands
-// sit in a shared-memory ring of three 32-band chunks, the next two always
-// on their way (cp.async); the band moves of the current and next chunk are
-// kept as one 64-bit word, so a step needs one shared-memory load.
+// until an index leaves the matrix; pair t of the walk goes to out[cap-1-t]
+// (t < cap).  Returns 0, or -1 if a traced cell lies outside its band (cannot
+// happen); n_out = pairs walked.  The records of 96 bands sit in a
+// shared-memory ring of three 32-band chunks, the next two always on their
+// way (cp.async).  Within a chunk a step is one shared-memory load and a
+// few bit operations: the band moves of this chunk and the next sit in two
+// words (one funnel shift gives the two that a step needs), and the step's
+// two index decrements are appended to two bit masks.  At the end of each
+// chunk the warp writes the chunk's pairs at once, lane t the t-th, its
+// indices from the masks' prefix counts.
 // Record layout: per-warp mode, offset j is bit j/C of word pair j%C of a
 // record of R words; block mode (GROUP), offset j = gw*W' + C*lane + i is
 // bit lane of word pair gw*C + i, W' = wg (wg_magic = ceil(2^32 / wg)).
@@ -719,56 +723,67 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
     chunk_copy<R>(r, top - 2 * kChunk, bufs + 2 * kChunk * R);
     cp_async_wait<1>();
     __syncwarp();
-    // bit i: band top-i moved by one event
-    unsigned long long em = (unsigned long long)chunk_event_moves<R, FULLW>(r, top, bufs) |
-                            ((unsigned long long)chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + kChunk * R)
-                             << 32);
-    const bool writer = r.lane == 0;
+    // bit i: band top-i (em_lo) or top-32-i (em_hi) moved by one event
+    unsigned em_lo = chunk_event_moves<R, FULLW>(r, top, bufs);
+    unsigned em_hi = chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + kChunk * R);
     int le = le_end;
     int off = 0;                       // the current cell's band is top - off
-    int n = 0;
-    unsigned bad = 0;
-    while (((e | k) >= 0) && !bad) {
-        const int j = le - e;
-        bad = (unsigned)j >= (unsigned)r.W ? 1u : 0u;
-        int p = base + off;
-        p -= (p >= RING) ? RING : 0;
-        unsigned pair, bit;
-        if (GROUP) {
-            const unsigned ju = bad ? 0u : (unsigned)j;          // keeps the load inside the record
-            const unsigned gq = __umulhi(ju, wg_magic);          // ju / wg
-            const unsigned jj = ju - gq * wg;
-            pair = gq * C + jj % C;
-            bit = jj / C;
-        } else {
-            pair = (unsigned)j % C;
-            bit = (unsigned)j / C;
+    int n = 0;                         // pairs walked before the current chunk
+    bool bad = false;
+    for (;;) {
+        const uint32_t *rec = bufs + base * R;
+        const int e0 = e, k0 = k;
+        unsigned de_bits = 0, dk_bits = 0;
+        int nb = 0;
+        while (off < kChunk && (e | k) >= 0) {     // at most 32 steps (each leaves at least one band)
+            const int j = le - e;
+            const bool out_of_band = (unsigned)j >= (unsigned)r.W;
+            bad |= out_of_band;
+            unsigned pair, bit;
+            if (GROUP) {
+                const unsigned ju = out_of_band ? 0u : (unsigned)j;   // keeps the load inside the record
+                const unsigned gq = __umulhi(ju, wg_magic);           // ju / wg
+                const unsigned jj = ju - gq * wg;
+                pair = gq * C + jj % C;
+                bit = jj / C;
+            } else {
+                pair = (unsigned)j % C;
+                bit = (unsigned)j / C;
+            }
+            const uint2 w = *reinterpret_cast<const uint2 *>(rec + off * R + 2 * pair);
+            const unsigned l = (w.y >> bit) & 1u;
+            const unsigned d = (((w.x >> bit) | l) & 1u) ^ 1u;      // D: neither L nor U
+            const unsigned ev = __funnelshift_r(em_lo, em_hi, off);  // bit 0: band top-off, bit 1: the one below
+            le -= (int)((ev & 1u) + ((ev >> 1) & d));
+            const unsigned de = l ^ 1u, dk = l | d;                 // U or D: e-1; L or D: k-1
+            e -= (int)de;
+            k -= (int)dk;
+            de_bits |= de << nb;
+            dk_bits |= dk << nb;
+            nb++;
+            off += 1 + (int)d;
         }
-        const uint2 w = *reinterpret_cast<const uint2 *>(bufs + p * R + 2 * pair);
-        if (writer && n < cap) out[cap - 1 - n] = make_int2(e, k);
-        n++;
-        const unsigned l = (w.y >> bit) & 1u;
-        const unsigned d = ((w.x >> bit) & 1u | l) ^ 1u;          // D: neither L nor U
-        const unsigned ev = (unsigned)(em >> off);                 // bit 0: band bb, bit 1: band bb-1
-        le -= (int)((ev & 1u) + ((ev >> 1) & d));
-        e -= (int)(l ^ 1u);                                        // U or D
-        k -= (int)(l | d);                                         // L or D
-        off += 1 + (int)d;
-        if (off >= kChunk) {           // the walk enters the next chunk
-            __syncwarp();
-            const int freed = base;
-            top -= kChunk;
-            off -= kChunk;
-            base += kChunk;
-            base -= (base >= RING) ? RING : 0;
-            em >>= 32;
-            cp_async_wait<0>();
-            __syncwarp();
-            int nxt = base + kChunk;
-            nxt -= (nxt >= RING) ? RING : 0;
-            em |= (unsigned long long)chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + nxt * R) << 32;
-            chunk_copy<R>(r, top - 2 * kChunk, bufs + freed * R);
+        if (r.lane < nb) {             // the chunk's pairs, one per lane
+            const unsigned below = (1u << r.lane) - 1u;
+            const int t = n + r.lane;
+            if (t < cap) out[cap - 1 - t] = make_int2(e0 - __popc(de_bits & below), k0 - __popc(dk_bits & below));
         }
+        n += nb;
+        if ((e | k) < 0 || bad) break;
+        // the walk enters the next chunk
+        __syncwarp();
+        const int freed = base;
+        top -= kChunk;
+        off -= kChunk;
+        base += kChunk;
+        base -= (base >= RING) ? RING : 0;
+        em_lo = em_hi;
+        cp_async_wait<0>();
+        __syncwarp();
+        int nxt = base + kChunk;
+        nxt -= (nxt >= RING) ? RING : 0;
+        em_hi = chunk_event_moves<R, FULLW>(r, top - kChunk, bufs + nxt * R);
+        chunk_copy<R>(r, top - 2 * kChunk, bufs + freed * R);
     }
     cp_async_wait<0>();
     __syncwarp();
