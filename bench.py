@@ -9,7 +9,7 @@ per second (GCUPS: in-matrix cells filled, summed over reads), also reported
 as reads/s.
 
   value : device-resident inputs (abea_align_batch_device); K steps spread
-          round-robin over D contexts, each on its own stream (D = 3 batches
+          round-robin over D contexts, each on its own stream (D = 6 batches
           in flight by default, so one batch's longest reads overlap the next
           batches' work), CUDA events around all K steps.
   e2e   : the same metric through abea_align_packed with page-locked host
@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--depth", type=int, default=3, help="batches in flight (one context and stream each)")
+    p.add_argument("--depth", type=int, default=6, help="batches in flight (one context and stream each)")
     p.add_argument("--serve-requests", type=int, default=500,
                    help="serve_mix requests at 1x offered load (4x as many at 10x); 0 skips serving")
     p.add_argument("--block-theta", type=float, default=0.0,
