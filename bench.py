@@ -44,9 +44,9 @@ METRIC = "ABEA band-cell updates/s (GCUPS) and reads/s on 1 GB300; p50/p99 laten
 UNIT = "GCUPS"
 OPS_PER_CELL = 10   # FP32-pipe ops of the canonical cell: 2 FFMA, 4 FADD, 2 compare, 2 select
 # DRAM bytes (read + write) per band of the core kernel from one ncu capture
-# (profiles/align_kernel_1024reads_sections.md), valid only for the kernel
+# (profiles/align_kernel_bulk_reads_le15kb_sections.md), valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.
-TRAFFIC_CAPTURE = {"source_sha1": "805c501b3761c6c655d7a8e3e3d66d3aa262be13", "bytes_per_band": 76.05}
+TRAFFIC_CAPTURE = {"source_sha1": "a220cd1c25541d3e5aa94f31e077012a3d3982d9", "bytes_per_band": 84.7}
 
 
 def parse():
@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--reads", type=int, default=None, help="only the first N reads of the workload (profiling)")
+    p.add_argument("--max-bases", type=int, default=None,
+                   help="only the workload's reads of at most this many bases (profiling the full-load mix)")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -295,7 +297,11 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    batch = synth.make_batch(args.workload, n_reads=args.reads)
+    if args.max_bases:
+        L = synth.read_lengths(synth.WORKLOADS[args.workload])
+        batch = synth.make_batch(args.workload, read_ids=np.nonzero(L <= args.max_bases)[0])
+    else:
+        batch = synth.make_batch(args.workload, n_reads=args.reads)
     n = batch.n
     D = max(1, args.depth)
     pair_off = binding.pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
