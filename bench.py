@@ -454,6 +454,32 @@ def run_ours(args):
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
 
+    # the per-read scaling estimate (method of moments) over the same batch, device-resident: a
+    # bandwidth-bound pass (4 B per event, 1 B per base, the model rows from L2)
+    d_sc = torch.zeros(n * 3, dtype=torch.float32, device=dev)
+    d_sst = torch.zeros(n, dtype=torch.int32, device=dev)
+
+    def scal():
+        ctxs[0].estimate_scalings(n, d_seq, batch.seq_off, d_ev, batch.ev_off, d_sc, d_sst,
+                                  stream=streams[0].cuda_stream)
+
+    for _ in range(3):
+        scal()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(streams[0])
+    for _ in range(args.steps):
+        scal()
+    s1.record(streams[0])
+    s1.synchronize()
+    scal_ms = s0.elapsed_time(s1) / args.steps
+    scal_bytes = int(batch.events.nbytes + batch.seq.nbytes)
+    hbm = float(measured_peaks().get("hbm_gbs") or 6800.0)
+    scalings_line = {"kernel": "scalings_kernel", "ms_per_launch": scal_ms, "reads_per_s": n / (scal_ms / 1e3),
+                     "roofline": {"bound": "hbm", "achieved": scal_bytes / (scal_ms / 1e3) / 1e9,
+                                  "peak": hbm, "unit": "GB/s",
+                                  "frac": scal_bytes / (scal_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": scal_bytes},
+                     "ok_reads": int((d_sst == 0).sum().item())}
+
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = [serve_latency(binding, synth, local_rank, load, n_req, 1.0)
@@ -481,7 +507,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
                         "host_threads": D},
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving,
+                "scalings_estimate": scalings_line}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

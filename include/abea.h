@@ -49,6 +49,11 @@ extern "C" {
 #define ABEA_READ_BAD_INPUT 2    /* non-ACGT base, non-finite event, var <= 0, no events, or seq shorter than k */
 #define ABEA_READ_CAPACITY 3     /* the read's pair capacity is smaller than its alignment (n_pairs = required) */
 
+/* Per-read status of abea_estimate_scalings. */
+#define ABEA_SCALE_OK 0          /* scale and shift from the moments */
+#define ABEA_SCALE_DEGENERATE 1  /* fewer than 2 events or a zero variance: scale 1, shift = mean difference */
+#define ABEA_SCALE_BAD_INPUT 2   /* no events or k-mers, non-ACGT base or non-finite event: scale 1, shift 0 */
+
 typedef struct abea_ctx abea_ctx;
 
 /* Read-model scaling (thesis Sec. ABEA, "read-model scaling"): the model
@@ -147,6 +152,21 @@ int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
  * then resets both counters.  Up to 4096 core-kernel launches are timed
  * between two calls (later ones are folded into the last slot). */
 int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
+
+/* Per-read scalings by the method of moments (thesis Sec. "Read-model
+ * scaling": shift and scale are estimated per read before ABEA, which then
+ * uses mu * scale + shift; the thesis gives no formula).  For read i, with
+ * m_e, v_e the mean and population variance of its event means and m_m, v_m
+ * those of the model level means (ctx's model) along its k-mers:
+ *   d_out[i] = { scale = sqrt(v_e / v_m), shift = m_e - scale * m_m, var = 1 },
+ * d_status[i] = ABEA_SCALE_OK; degenerate and rejected reads as the
+ * ABEA_SCALE_* codes say.  Computed in FP64, rounded once to float.  Bulk data
+ * as in abea_align_batch_device: d_seq, d_events, d_out (abea_scalings[n])
+ * and d_status (int32[n]) are device pointers, seq_off and ev_off host
+ * arrays; enqueued on cuda_stream without waiting. */
+int abea_estimate_scalings(abea_ctx *ctx, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,
+                           const float *d_events, const int64_t *ev_off, abea_scalings *d_out,
+                           int32_t *d_status, void *cuda_stream);
 
 /* Scheduling of long reads (the paper has no counterpart; results do not
  * depend on it).  Within one core-kernel launch a read normally occupies one

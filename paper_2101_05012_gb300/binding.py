@@ -24,11 +24,12 @@ ABEA_ERR_TIMEOUT = -5
 ABEA_ERR_NO_MODEL = -6
 
 READ_OK, READ_FAIL_NO_END, READ_BAD_INPUT, READ_CAPACITY = range(4)
+SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
-           "abea_set_block_mode", "abea_server_start", "abea_server_submit", "abea_server_poll",
+           "abea_set_block_mode", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
            "abea_server_stop", "abea_align_batch_device_noalloc"]
 
 
@@ -90,6 +91,7 @@ def load(path: Optional[str] = None):
     lib.abea_align_batch_device.argtypes = [P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
     lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.abea_set_block_mode.argtypes = [P, ctypes.c_double]
+    lib.abea_estimate_scalings.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.abea_server_start.argtypes = [P, ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
     lib.abea_server_submit.argtypes = [P, ctypes.POINTER(Read), ctypes.POINTER(i64)]
     lib.abea_server_poll.argtypes = [P, i64, i32, ctypes.POINTER(Result), P, i32, ctypes.POINTER(ctypes.c_double)]
@@ -209,6 +211,16 @@ class Context:
             self.h, n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
             _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
             ctypes.c_void_p(stream)), "abea_align_batch_device")
+
+    def estimate_scalings(self, n: int, d_seq, seq_off, d_events, ev_off, d_out, d_status, stream=None):
+        """abea_estimate_scalings: d_* are torch CUDA tensors (uint8 bases, float32 events, float32[n*3]
+        scalings out, int32[n] status out); offsets are host numpy arrays."""
+        so = np.ascontiguousarray(seq_off, np.int64)
+        eo = np.ascontiguousarray(ev_off, np.int64)
+        _check(self.lib.abea_estimate_scalings(
+            self.h, n, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
+            ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_status.data_ptr()), ctypes.c_void_p(stream)),
+            "abea_estimate_scalings")
 
     def set_block_mode(self, theta: float):
         """Reads above theta x the even per-warp share of bands run on a whole block (<= 0: never)."""

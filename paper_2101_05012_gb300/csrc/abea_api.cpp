@@ -52,9 +52,9 @@ struct abea_ctx {
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
     DevBuf model;
-    DevBuf rd, order, flags, kc, trace, moves, queue;
+    DevBuf rd, order, flags, kc, trace, moves, queue, offs;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
-    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs;
+    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
@@ -405,9 +405,9 @@ void abea_destroy(abea_ctx *c)
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     cudaDeviceSynchronize();
     DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
-                     &c->queue, &c->events, &c->seq, &c->res, &c->pairs};
+                     &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs};
     for (DevBuf *b : dev) free_dev(*b);
-    HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs};
+    HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs};
     for (HostBuf *b : host) free_host(*b);
     for (cudaEvent_t e : c->wave_t0) cudaEventDestroy(e);
     for (cudaEvent_t e : c->wave_t1) cudaEventDestroy(e);
@@ -633,6 +633,40 @@ int abea_align(abea_ctx *c, const abea_read *read, int W, abea_result *out, int3
     int rc = abea_align_batch(c, read, 1, W, out, pairs, po, nullptr);
     if (rc) return rc;
     if (out->status == ABEA_READ_CAPACITY) return ABEA_ERR_CAPACITY;
+    return ABEA_OK;
+}
+
+int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,
+                           const float *d_events, const int64_t *ev_off, abea_scalings *d_out, int32_t *d_status,
+                           void *cuda_stream)
+{
+    if (!c) return ABEA_ERR_ARG;
+    if (c->k <= 0) return ABEA_ERR_NO_MODEL;
+    if (n < 0 || (n > 0 && (!seq_off || !ev_off || !d_out || !d_status || !d_seq || !d_events))) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    for (int32_t i = 0; i < n; i++)
+        if (seq_off[i + 1] < seq_off[i] || ev_off[i + 1] < ev_off[i] || seq_off[i + 1] - seq_off[i] > INT32_MAX ||
+            ev_off[i + 1] - ev_off[i] > INT32_MAX)
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    int rc;
+    // the offsets go through page-locked staging (free once its previous upload is done)
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    const size_t bytes = 2 * (size_t)(n + 1) * sizeof(int64_t);
+    if ((rc = ensure_host(c->h_offs, bytes))) return rc;
+    if ((rc = ensure_dev(c, c->offs, bytes))) return rc;
+    int64_t *h = (int64_t *)c->h_offs.p;
+    std::memcpy(h, seq_off, (size_t)(n + 1) * sizeof(int64_t));
+    std::memcpy(h + n + 1, ev_off, (size_t)(n + 1) * sizeof(int64_t));
+    if ((rc = cuda_err(cudaMemcpyAsync(c->offs.p, h, bytes, cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
+    const int64_t *d_off = (const int64_t *)c->offs.p;
+    if ((rc = cuda_err((cudaError_t)abea::launch_scalings(d_off, d_off + n + 1, n, d_seq, d_events,
+                                                           (const ModelRow *)c->model.p, c->k, d_out, d_status,
+                                                           st))))
+        return rc;
+    c->last_launches++;
     return ABEA_OK;
 }
 

@@ -69,6 +69,9 @@ struct AlignArgs {
 int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *events,
                 const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
 int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream);
+int launch_scalings(const int64_t *d_seq_off, const int64_t *d_ev_off, int32_t n, const uint8_t *seq,
+                    const float *events, const ModelRow *model, int k, abea_scalings *out, int32_t *status,
+                    void *stream);
 int align_grid_size(const Geometry &g, int device);
 
 constexpr double kDefaultBlockTheta = 1.0;
