@@ -735,14 +735,15 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
         const int e0 = e, k0 = k;
         unsigned de_bits = 0, dk_bits = 0;
         int nb = 0;
-        while (off < kChunk && (e | k) >= 0) {     // at most 32 steps (each leaves at least one band)
+        // One step of the walk.  A cell outside its band (it cannot happen) is noted at the end of
+        // the chunk from the largest offset seen; the load index stays inside the record either way.
+        unsigned jmax = 0;
+        auto step = [&]() {
             const int j = le - e;
-            const bool out_of_band = (unsigned)j >= (unsigned)r.W;
-            bad |= out_of_band;
             unsigned pair, bit;
             if (GROUP) {
-                const unsigned ju = out_of_band ? 0u : (unsigned)j;   // keeps the load inside the record
-                const unsigned gq = __umulhi(ju, wg_magic);           // ju / wg
+                const unsigned ju = ((unsigned)j >= (unsigned)r.W) ? 0u : (unsigned)j;   // inside the record
+                const unsigned gq = __umulhi(ju, wg_magic);                           // ju / wg
                 const unsigned jj = ju - gq * wg;
                 pair = gq * C + jj % C;
                 bit = jj / C;
@@ -750,6 +751,7 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
                 pair = (unsigned)j % C;
                 bit = (unsigned)j / C;
             }
+            jmax = max(jmax, (unsigned)j);
             const uint2 w = *reinterpret_cast<const uint2 *>(rec + off * R + 2 * pair);
             const unsigned l = (w.y >> bit) & 1u;
             const unsigned d = (((w.x >> bit) | l) & 1u) ^ 1u;      // D: neither L nor U
@@ -762,7 +764,13 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
             dk_bits |= dk << nb;
             nb++;
             off += 1 + (int)d;
+        };
+        while (off <= kChunk - 4 && e >= 1 && k >= 1) {      // two steps stay in the chunk and the matrix
+            step();
+            step();
         }
+        while (off < kChunk && (e | k) >= 0) step();         // at most 32 steps in all per chunk
+        bad |= jmax >= (unsigned)r.W;
         if (r.lane < nb) {             // the chunk's pairs, one per lane
             const unsigned below = (1u << r.lane) - 1u;
             const int t = n + r.lane;
