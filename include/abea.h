@@ -191,7 +191,8 @@ int abea_set_block_mode(abea_ctx *ctx, double theta);
  *
  * A worker thread closes a micro-batch when it holds max_batch_reads
  * requests or max_wait_us after its first request arrived, whichever comes
- * first, and runs it on one of batches_in_flight internal contexts (each
+ * first (short reads and longer ones batch apart, see short_bases), and runs
+ * it on one of batches_in_flight internal contexts (each
  * with its own stream and page-locked staging) on ctx's device, with ctx's
  * model; each internal context gets 1/batches_in_flight of ctx's memory
  * budget, and a micro-batch stays within it.  Results equal those of
@@ -205,6 +206,9 @@ typedef struct {
     int32_t batches_in_flight; /* 0: 3 */
     int32_t max_requests;      /* 0: 65536; requests submitted and not yet polled to completion */
     double block_theta;        /* per micro-batch, as abea_set_block_mode (<= 0: off) */
+    int32_t short_bases;       /* 0: 1000; reads of at most this many bases queue and batch apart, go
+                                  first and may use every context, longer ones leave one context free
+                                  for them; < 0: one queue for all */
 } abea_server_cfg;
 
 /* Returns ABEA_ERR_NO_MODEL if ctx has no model, ABEA_ERR_ARG for a bad cfg. */

@@ -45,7 +45,7 @@ class Read(ctypes.Structure):
 class ServerCfg(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int), ("max_batch_reads", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
                 ("batches_in_flight", ctypes.c_int32), ("max_requests", ctypes.c_int32),
-                ("block_theta", ctypes.c_double)]
+                ("block_theta", ctypes.c_double), ("short_bases", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -237,10 +237,12 @@ class Server:
     """abea_server_*: continuous admission of single-read requests on a Context's device and model."""
 
     def __init__(self, ctx: Context, W: int, max_batch_reads: int = 0, max_wait_us: int = 0,
-                 batches_in_flight: int = 0, max_requests: int = 0, block_theta: float = 1.0):
+                 batches_in_flight: int = 0, max_requests: int = 0, block_theta: float = 1.0,
+                 short_bases: int = 0):
         self.lib = ctx.lib
         self.k = ctx.k
-        cfg = ServerCfg(W, max_batch_reads, max_wait_us, batches_in_flight, max_requests, float(block_theta))
+        cfg = ServerCfg(W, max_batch_reads, max_wait_us, batches_in_flight, max_requests, float(block_theta),
+                        short_bases)
         h = ctypes.c_void_p()
         _check(self.lib.abea_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h)), "abea_server_start")
         self.h = h

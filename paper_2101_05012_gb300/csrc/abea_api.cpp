@@ -62,6 +62,8 @@ struct abea_ctx {
     std::vector<float> h_mean, h_stdv;          // the model as set (host copy)
     int grid[9][2][2][3] = {};
     double block_theta = abea::kDefaultBlockTheta;   // block mode for reads above theta x the even share
+    cudaMemPool_t pool = nullptr;               // the working buffers (stream-ordered: growing one never
+                                                // synchronises the device)
 };
 
 namespace {
@@ -73,21 +75,24 @@ int cuda_err(cudaError_t e)
     return ABEA_ERR_CUDA;
 }
 
-int ensure_dev(abea_ctx *c, DevBuf &b, size_t bytes)
+// Grow a working buffer, in stream order on st (the stream is already ordered
+// after every earlier use of the buffer).
+int ensure_dev(abea_ctx *c, DevBuf &b, size_t bytes, cudaStream_t st)
 {
     if (bytes <= b.cap) return ABEA_OK;
     size_t want = std::max(bytes, b.cap + b.cap / 4);
     want = (want + 255) & ~size_t(255);
     if (b.p) {
-        cudaFree(b.p);
+        cudaFreeAsync(b.p, st);
         c->held -= b.cap;
         b.p = nullptr;
         b.cap = 0;
     }
-    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&b.p, want, c->pool, st) != cudaSuccess) {
         cudaGetLastError();
-        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&b.p, bytes, c->pool, st) != cudaSuccess) {
             cudaGetLastError();
+            b.p = nullptr;
             return ABEA_ERR_NOMEM;
         }
         want = bytes;
@@ -219,13 +224,13 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
              int32_t *d_pairs, int W, cudaStream_t st)
 {
     int rc;
-    if ((rc = ensure_dev(c, c->rd, (size_t)n * sizeof(ReadDesc)))) return rc;
-    if ((rc = ensure_dev(c, c->order, (size_t)n * sizeof(int32_t)))) return rc;
-    if ((rc = ensure_dev(c, c->flags, (size_t)n * sizeof(int32_t)))) return rc;
-    if ((rc = ensure_dev(c, c->kc, std::max<size_t>(f.kc, 1) * 16))) return rc;
-    if ((rc = ensure_dev(c, c->trace, std::max<size_t>(f.trace, 4) * 4))) return rc;
-    if ((rc = ensure_dev(c, c->moves, std::max<size_t>(f.moves, 16)))) return rc;
-    if ((rc = ensure_dev(c, c->queue, 256))) return rc;
+    if ((rc = ensure_dev(c, c->rd, (size_t)n * sizeof(ReadDesc), st))) return rc;
+    if ((rc = ensure_dev(c, c->order, (size_t)n * sizeof(int32_t), st))) return rc;
+    if ((rc = ensure_dev(c, c->flags, (size_t)n * sizeof(int32_t), st))) return rc;
+    if ((rc = ensure_dev(c, c->kc, std::max<size_t>(f.kc, 1) * 16, st))) return rc;
+    if ((rc = ensure_dev(c, c->trace, std::max<size_t>(f.trace, 4) * 4, st))) return rc;
+    if ((rc = ensure_dev(c, c->moves, std::max<size_t>(f.moves, 16), st))) return rc;
+    if ((rc = ensure_dev(c, c->queue, 256, st))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->rd.p, h_rd, (size_t)n * sizeof(ReadDesc), cudaMemcpyHostToDevice, st))))
         return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->order.p, h_order, (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st))))
@@ -320,10 +325,10 @@ int packed_direct(abea_ctx *c, const Geometry &g, int32_t n, int W, const char *
     }
     Footprint f;
     plan_reads(c, g, ids, seq_off, ev_off, sc, sb, eb, pb, pc, (ReadDesc *)c->h_rd.p, (int32_t *)c->h_order.p, f);
-    if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1)))) return rc;
-    if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4))) return rc;
-    if ((rc = ensure_dev(c, c->res, (size_t)n * sizeof(abea_result)))) return rc;
-    if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8))) return rc;
+    if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1), st))) return rc;
+    if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4, st))) return rc;
+    if ((rc = ensure_dev(c, c->res, (size_t)n * sizeof(abea_result), st))) return rc;
+    if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8, st))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->seq.p, seq + seq_off[0], (size_t)ns, cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->events.p, events + ev_off[0], 4 * (size_t)ne, cudaMemcpyHostToDevice, st))))
         return rc;
@@ -392,6 +397,17 @@ int abea_create(abea_ctx **out, int device, size_t mem_budget_bytes)
         abea_destroy(c);
         return cuda_err(cudaErrorUnknown);
     }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    uint64_t keep = ~(uint64_t)0;                     // keep freed memory for the next growth
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        cudaGetLastError();
+        abea_destroy(c);
+        return ABEA_ERR_CUDA;
+    }
     c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.9 * (double)free_b);
     cudaEventRecord(c->batch_done, c->own_stream);
     *out = c;
@@ -416,6 +432,7 @@ void abea_destroy(abea_ctx *c)
     if (c->upload_done) cudaEventDestroy(c->upload_done);
     if (c->batch_done) cudaEventDestroy(c->batch_done);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     cudaGetLastError();
     delete c;
 }
@@ -573,10 +590,10 @@ int abea_align_packed(abea_ctx *c, int32_t n, int W, const char *seq, const int6
         Footprint f;
         plan_reads(c, g, loc, s_off.data(), e_off.data(), wsc.data(), sb, eb, pb, pc, (ReadDesc *)c->h_rd.p,
                    (int32_t *)c->h_order.p, f);
-        if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1)))) return rc;
-        if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4))) return rc;
-        if ((rc = ensure_dev(c, c->res, (size_t)m * sizeof(abea_result)))) return rc;
-        if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8))) return rc;
+        if ((rc = ensure_dev(c, c->seq, std::max<int64_t>(ns, 1), st))) return rc;
+        if ((rc = ensure_dev(c, c->events, std::max<int64_t>(ne, 1) * 4, st))) return rc;
+        if ((rc = ensure_dev(c, c->res, (size_t)m * sizeof(abea_result), st))) return rc;
+        if ((rc = ensure_dev(c, c->pairs, std::max<int64_t>(np, 1) * 8, st))) return rc;
         if ((rc = cuda_err(cudaMemcpyAsync(c->seq.p, c->h_seq.p, (size_t)ns, cudaMemcpyHostToDevice, st)))) return rc;
         if ((rc = cuda_err(cudaMemcpyAsync(c->events.p, c->h_events.p, 4 * (size_t)ne, cudaMemcpyHostToDevice, st))))
             return rc;
@@ -651,11 +668,12 @@ int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const i
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
     cudaStream_t st = pick_stream(c, cuda_stream);
     int rc;
+    if ((rc = order_after_previous(c, st))) return rc;
     // the offsets go through page-locked staging (free once its previous upload is done)
     if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
     const size_t bytes = 2 * (size_t)(n + 1) * sizeof(int64_t);
     if ((rc = ensure_host(c->h_offs, bytes))) return rc;
-    if ((rc = ensure_dev(c, c->offs, bytes))) return rc;
+    if ((rc = ensure_dev(c, c->offs, bytes, st))) return rc;
     int64_t *h = (int64_t *)c->h_offs.p;
     std::memcpy(h, seq_off, (size_t)(n + 1) * sizeof(int64_t));
     std::memcpy(h + n + 1, ev_off, (size_t)(n + 1) * sizeof(int64_t));
@@ -667,7 +685,7 @@ int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const i
                                                            st))))
         return rc;
     c->last_launches++;
-    return ABEA_OK;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
 }
 
 int abea_set_block_mode(abea_ctx *c, double theta)

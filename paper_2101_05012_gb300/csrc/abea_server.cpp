@@ -4,7 +4,8 @@
 // The thesis aligns files batch by batch (Sec. "Data array serialisation"
 // packs a batch, one launch per batch); a server cannot wait for a full
 // batch.  Here a worker thread closes a micro-batch when it holds
-// max_batch_reads requests or max_wait_us after its oldest request arrived,
+// max_batch_reads requests or max_wait_us after its oldest request arrived
+// (short reads and longer ones queue and batch apart; see run()),
 // takes the first internal context whose previous micro-batch has finished,
 // packs the requests into that context's page-locked staging and enqueues
 // the whole path (copies in, pre-kernel, core kernel, copies out) on the
@@ -12,7 +13,7 @@
 // copies out (cudaLaunchHostFunc; it calls no CUDA API) moves each result to
 // its request, stamps the completion time and frees the context.  While a
 // micro-batch with long reads is running, later requests run on the other
-// contexts, so short requests do not wait behind long ones.
+// contexts, and one context is always left for short requests.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -95,24 +96,17 @@ struct abea_server {
     size_t budget = 0;                 // per internal context
     std::vector<Request> table;        // max_requests entries; index = ticket % max_requests
     std::vector<int32_t> free_idx;
-    std::deque<int32_t> fifo;          // queued requests, oldest first
+    std::deque<int32_t> fifo[2];       // queued requests, oldest first: [0] short reads, [1] the others
     std::vector<Slot> slots;
     std::mutex m;
-    std::condition_variable cv_work;   // a request was queued, or stop
-    std::condition_variable cv_done;   // a micro-batch finished
+    std::condition_variable cv_work;   // the worker: a request was queued, a micro-batch finished, or stop
+    std::condition_variable cv_done;   // pollers: a micro-batch finished
     std::thread worker;
     bool stopping = false;
     int64_t serial = 0;
 };
 
 namespace {
-
-bool any_free(const abea_server *s)
-{
-    for (const Slot &x : s->slots)
-        if (!x.busy) return true;
-    return false;
-}
 
 bool all_free(const abea_server *s)
 {
@@ -141,6 +135,7 @@ void CUDART_CB batch_done(void *arg)
         slot->busy = false;
     }
     s->cv_done.notify_all();
+    s->cv_work.notify_one();
 }
 
 // Pack the slot's requests and enqueue their micro-batch (no lock held; the
@@ -183,33 +178,62 @@ int launch(abea_server *s, Slot &slot)
     return ABEA_OK;
 }
 
+int free_slots(const abea_server *s)
+{
+    int f = 0;
+    for (const Slot &x : s->slots) f += x.busy ? 0 : 1;
+    return f;
+}
+
+// The worker.  Short reads (at most short_bases bases) and the others queue
+// apart and form their own micro-batches; a queue's micro-batch closes when it
+// holds max_batch_reads requests or max_wait_us after its oldest request.
+// Short micro-batches go first and may take any free context; the others
+// leave one context free for them (unless there is only one), so a short
+// request never waits behind a context full of long reads.
 void run(abea_server *s)
 {
     cudaSetDevice(s->device);
+    const std::chrono::microseconds wait(s->cfg.max_wait_us);
     std::unique_lock<std::mutex> lk(s->m);
     for (;;) {
-        s->cv_work.wait(lk, [&] { return s->stopping || !s->fifo.empty(); });
-        if (s->fifo.empty()) break;                       // stopping, nothing queued
-        const Clock::time_point close_at =
-            s->table[s->fifo.front()].t_submit + std::chrono::microseconds(s->cfg.max_wait_us);
-        while (!s->stopping && (int32_t)s->fifo.size() < s->cfg.max_batch_reads && Clock::now() < close_at)
-            s->cv_work.wait_until(lk, close_at);
-        s->cv_done.wait(lk, [&] { return any_free(s); });
+        if (s->fifo[0].empty() && s->fifo[1].empty()) {
+            if (s->stopping) break;
+            s->cv_work.wait(lk);
+            continue;
+        }
+        const Clock::time_point now = Clock::now();
+        Clock::time_point next = Clock::time_point::max();
+        int cls = -1;
+        for (int c = 0; c < 2 && cls < 0; c++) {
+            if (s->fifo[c].empty()) continue;
+            const Clock::time_point close_at = s->table[s->fifo[c].front()].t_submit + wait;
+            const bool ready = s->stopping || (int32_t)s->fifo[c].size() >= s->cfg.max_batch_reads || now >= close_at;
+            const int need = (c == 1 && s->cfg.short_bases >= 0 && (int)s->slots.size() > 1) ? 2 : 1;
+            if (ready && free_slots(s) >= need) cls = c;
+            else if (!ready) next = std::min(next, close_at);
+        }
+        if (cls < 0) {                                    // nothing to start: wait for a close time, a request or a context
+            if (next == Clock::time_point::max()) s->cv_work.wait(lk);
+            else s->cv_work.wait_until(lk, next);
+            continue;
+        }
         Slot *slot = nullptr;
         for (Slot &x : s->slots)
             if (!x.busy) {
                 slot = &x;
                 break;
             }
+        std::deque<int32_t> &q = s->fifo[cls];
         slot->reqs.clear();
         size_t bytes = 0;
-        while (!s->fifo.empty() && (int32_t)slot->reqs.size() < s->cfg.max_batch_reads) {
-            Request &r = s->table[s->fifo.front()];
+        while (!q.empty() && (int32_t)slot->reqs.size() < s->cfg.max_batch_reads) {
+            Request &r = s->table[q.front()];
             if (!slot->reqs.empty() && bytes + r.bytes > s->budget) break;
             bytes += r.bytes;
             r.state = State::Running;
-            slot->reqs.push_back(s->fifo.front());
-            s->fifo.pop_front();
+            slot->reqs.push_back(q.front());
+            q.pop_front();
         }
         slot->busy = true;
         lk.unlock();
@@ -226,7 +250,7 @@ void run(abea_server *s)
             s->cv_done.notify_all();
         }
     }
-    s->cv_done.wait(lk, [&] { return all_free(s); });
+    while (!all_free(s)) s->cv_work.wait(lk);
 }
 
 void retire(abea_server *s, int32_t idx)
@@ -256,6 +280,7 @@ int abea_server_start(abea_ctx *ctx, const abea_server_cfg *cfg, abea_server **o
     if (c.max_wait_us == 0) c.max_wait_us = 200;
     if (c.batches_in_flight == 0) c.batches_in_flight = 3;
     if (c.max_requests == 0) c.max_requests = 65536;
+    if (c.short_bases == 0) c.short_bases = 1000;
     if (c.W < 2 || c.W > 256 || c.max_batch_reads < 1 || c.max_batch_reads > (1 << 20) || c.max_wait_us < 0 ||
         c.batches_in_flight < 1 || c.batches_in_flight > 16 || c.max_requests < 1 || c.max_requests > (1 << 24) ||
         std::isnan(c.block_theta))
@@ -275,6 +300,11 @@ int abea_server_start(abea_ctx *ctx, const abea_server_cfg *cfg, abea_server **o
         x.srv = s;
         if ((rc = abea_create(&x.ctx, s->device, s->budget)) || (rc = abea_set_model(x.ctx, k, mean, stdv)) ||
             (rc = abea_set_block_mode(x.ctx, c.block_theta)))
+            break;
+        // page-locked staging for typical micro-batches up front: growing it later costs a free of
+        // page-locked memory while other micro-batches run
+        if ((rc = x.seq.reserve(size_t(4) << 20)) || (rc = x.ev.reserve(size_t(2) << 20)) ||
+            (rc = x.out.reserve(4096)) || (rc = x.pairs.reserve(size_t(4) << 20)))
             break;
     }
     if (rc != ABEA_OK) {
@@ -322,7 +352,7 @@ int abea_server_submit(abea_server *s, const abea_read *rd, int64_t *ticket)
         r.err = ABEA_OK;
         r.pairs.clear();
         r.t_submit = Clock::now();
-        s->fifo.push_back(idx);
+        s->fifo[(s->cfg.short_bases >= 0 && rd->seq_len <= s->cfg.short_bases) ? 0 : 1].push_back(idx);
         *ticket = r.ticket;
     }
     s->cv_work.notify_one();

@@ -72,6 +72,20 @@ def test_each_result_same_alone_and_in_the_mix(ctx, mix):
         assert np.array_equal(got[i][1], o["pairs"][o["pair_off"][t]:o["pair_off"][t] + o["n_pairs"][t]])
 
 
+def test_single_queue_gives_the_same_results(ctx, mix):
+    """short_bases < 0: one queue for all requests; the results do not change."""
+    batch = mix[0]
+    ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
+    ids = list(range(0, batch.n, 2))
+    got = {}
+    for sb in (0, -1):
+        with binding.Server(ctx, batch.W, max_batch_reads=16, max_wait_us=300, short_bases=sb) as srv:
+            got[sb] = collect(srv, submit_all(srv, batch, ids))
+    for i in ids:
+        assert np.float32(got[0][i][0]["score"]) == np.float32(got[-1][i][0]["score"])
+        assert np.array_equal(got[0][i][1], got[-1][i][1])
+
+
 def test_admission_under_memory_budget(mix):
     batch = mix[0]
     w = synth.WORKLOADS["batch_4096_ln5kb"]
