@@ -32,6 +32,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream tags
 _T_LEN, _T_ULTRA, _T_SEQ, _T_SKIP, _T_DWELL, _T_NOISE, _T_SCALE, _T_MODEL, _T_ARRIVAL, _T_CLASS = range(1, 11)
+_T_RAW_DWELL, _T_RAW_NOISE, _T_CALIB = range(11, 14)
 
 BASES = np.frombuffer(b"ACGT", dtype=np.uint8)
 
@@ -319,3 +320,86 @@ def custom_batch(events_list, seqs, scalings, model_mean, model_stdv, k, W, name
                  np.concatenate(sq) if sq else np.zeros(0, np.uint8), _offsets([len(s) for s in sq]),
                  np.concatenate(ev) if ev else np.zeros(0, np.float32), _offsets([len(e) for e in ev]),
                  np.asarray(scalings, dtype=np.float32).reshape(-1, 3), name)
+
+
+@dataclasses.dataclass
+class RawBatch:
+    """Raw signals of a batch (the input of event detection), packed.
+
+    raw: int16 ADC samples of all reads; read i is raw[raw_off[i]:raw_off[i+1]].
+    calib: float32[n, 2] = (offset, pA per ADC unit): pA = (raw + offset) * calib[:, 1].
+    starts: the true first sample of each k-mer of each read, packed like
+    start_off (for tests of the detector against the generator).
+    """
+    k: int
+    model_mean: np.ndarray
+    model_stdv: np.ndarray
+    seq: np.ndarray
+    seq_off: np.ndarray
+    raw: np.ndarray
+    raw_off: np.ndarray
+    calib: np.ndarray
+    starts: np.ndarray
+    start_off: np.ndarray
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return len(self.raw_off) - 1
+
+    def signal(self, i: int) -> np.ndarray:
+        return self.raw[self.raw_off[i]:self.raw_off[i + 1]]
+
+
+def make_raw_read(w: Workload, r: int, L: int, model_mean, model_stdv, samples_per_base: float = 4000.0 / 450.0):
+    """Bases, raw int16 signal, calibration and true k-mer starts of read r.
+
+    The read's bases and scalings are those of make_read.  Each k-mer holds
+    the pore for a geometric number of samples (mean samples_per_base, at
+    least one); every sample is scale*mean + shift + N(0, (stdv*var)^2) pA of
+    its k-mer, digitised as round(pA / pA_per_unit - offset) with a per-read
+    offset ~ U(-10, 10) and pA_per_unit = range / 8192, range ~ U(1350, 1450).
+    """
+    k = w.k
+    kseq = stream_key(w.seed, _T_SEQ, r)
+    words = draw_u64(kseq, np.arange((L + 31) // 32, dtype=np.uint64))
+    shifts = (np.arange(32, dtype=np.uint64) * np.uint64(2))
+    codes = ((words[:, None] >> shifts[None, :]) & np.uint64(3)).reshape(-1)[:L].astype(np.int64)
+    seq = BASES[codes]
+    rows = kmer_model_index(codes, k)
+    n_k = len(rows)
+    u = draw_unit(stream_key(w.seed, _T_SCALE, r), np.arange(3, dtype=np.uint64))
+    scale = w.scale_range[0] + (w.scale_range[1] - w.scale_range[0]) * u[0]
+    shift = w.shift_range[0] + (w.shift_range[1] - w.shift_range[0]) * u[1]
+    var = w.var_range[0] + (w.var_range[1] - w.var_range[0]) * u[2]
+    p = 1.0 / samples_per_base
+    ud = draw_open_unit(stream_key(w.seed, _T_RAW_DWELL, r), np.arange(n_k, dtype=np.uint64))
+    dwell = 1 + np.floor(np.log(ud) / np.log1p(-p)).astype(np.int64)
+    srows = np.repeat(rows, dwell)
+    z = draw_normal(stream_key(w.seed, _T_RAW_NOISE, r), np.arange(len(srows), dtype=np.uint64))
+    pa = scale * model_mean[srows].astype(np.float64) + shift + z * model_stdv[srows].astype(np.float64) * var
+    c = draw_unit(stream_key(w.seed, _T_CALIB, r), np.arange(2, dtype=np.uint64))
+    offset = -10.0 + 20.0 * c[0]
+    per_unit = (1350.0 + 100.0 * c[1]) / 8192.0
+    raw = np.clip(np.rint(pa / per_unit - offset), -32768, 32767).astype(np.int16)
+    starts = np.concatenate([[0], np.cumsum(dwell)[:-1]]).astype(np.int64)
+    return seq, raw, np.array([offset, per_unit], dtype=np.float32), starts
+
+
+def make_raw_batch(w, n_reads: Optional[int] = None, read_ids=None) -> RawBatch:
+    """Raw signals of a workload's reads (its lengths, model and seed)."""
+    w = WORKLOADS[w] if isinstance(w, str) else w
+    mm, ms = make_model(w.k, w.seed, w.level_mean_range, w.level_stdv_range)
+    L = read_lengths(w)
+    ids = np.arange(w.n_reads if n_reads is None else n_reads) if read_ids is None else np.asarray(read_ids)
+    seqs, raws, cals, sts = [], [], [], []
+    for r in ids:
+        s, x, c, st = make_raw_read(w, int(r), int(L[r]), mm, ms)
+        seqs.append(s)
+        raws.append(x)
+        cals.append(c)
+        sts.append(st)
+    return RawBatch(w.k, mm, ms, np.concatenate(seqs), _offsets([len(x) for x in seqs]),
+                    np.concatenate(raws), _offsets([len(x) for x in raws]), np.stack(cals),
+                    np.concatenate(sts), _offsets([len(x) for x in sts]), w.name)
+
