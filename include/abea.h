@@ -153,6 +153,31 @@ int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
  * between two calls (later ones are folded into the last slot). */
 int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
 
+/* Event detection: raw signal -> events (thesis Sec. "Methylation calling":
+ * the raw signal is segmented at sudden level changes, each segment an event
+ * with the mean, standard deviation and duration of its samples; the thesis
+ * gives no detector).  Two-window t-test: at sample position i of a read with
+ * exact window sums S_L, S_R (of x[i-window, i) and x[i, i+window)) and
+ * Q_L, Q_R of the squares, t2 = float(window*(S_R-S_L)^2) /
+ * float(window*(Q_L+Q_R) - S_L^2 - S_R^2) (+inf for a zero denominator and a
+ * nonzero numerator), 0 where a window leaves the read.  Position i >= 1
+ * starts an event when t2 >= tau2 and t2 is the maximum within
+ * window-1 positions on each side (ties to the earliest).  Each event:
+ * mean = float(S)/L, stdv = sqrt(max(float(Q)/L - mean^2, 0)) (FP32, in that
+ * order), both in pA: (mean + offset) * pa_per_unit, stdv * pa_per_unit.
+ * Starts are at least `window` samples apart, so a read of L samples has at
+ * most L/window + 1 events.  window in [2, 8]; defaults 3 and 2.0 give about
+ * 1.7 events per k-mer on the synthetic signals (the thesis reports 1.5-2.5).
+ * d_raw (int16 samples), d_events (event_off[n] entries) and d_n_events
+ * (int32[n]) are device pointers; raw_off, calib and event_off host arrays.
+ * d_n_events[i] is read i's event count; only its first
+ * event_off[i+1]-event_off[i] events are written. */
+typedef struct { float mean, stdv; int32_t start, length; } abea_event;   /* pA, pA, samples, samples */
+typedef struct { float offset, pa_per_unit; } abea_calib;                 /* pA = (raw + offset) * pa_per_unit */
+int abea_detect_events(abea_ctx *ctx, int32_t n, const int16_t *d_raw, const int64_t *raw_off,
+                       const abea_calib *calib, int window, float tau2, abea_event *d_events,
+                       const int64_t *event_off, int32_t *d_n_events, void *cuda_stream);
+
 /* Per-read scalings by the method of moments (thesis Sec. "Read-model
  * scaling": shift and scale are estimated per read before ABEA, which then
  * uses mu * scale + shift; the thesis gives no formula).  For read i, with

@@ -29,7 +29,7 @@ SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
-           "abea_set_block_mode", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
+           "abea_set_block_mode", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
            "abea_server_stop", "abea_align_batch_device_noalloc"]
 
 
@@ -52,6 +52,8 @@ class Result(ctypes.Structure):
     _fields_ = [("score", ctypes.c_float), ("status", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
                 ("e_end", ctypes.c_int32), ("cells", ctypes.c_int64)]
 
+
+EVENT_DTYPE = np.dtype([("mean", "<f4"), ("stdv", "<f4"), ("start", "<i4"), ("length", "<i4")])
 
 RESULT_DTYPE = np.dtype([("score", "<f4"), ("status", "<i4"), ("n_pairs", "<i4"), ("e_end", "<i4"),
                          ("cells", "<i8")])
@@ -92,6 +94,7 @@ def load(path: Optional[str] = None):
     lib.abea_last_launch_stats.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.abea_set_block_mode.argtypes = [P, ctypes.c_double]
     lib.abea_estimate_scalings.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.abea_detect_events.argtypes = [P, i32, P, P, P, ctypes.c_int, ctypes.c_float, P, P, P, P]
     lib.abea_server_start.argtypes = [P, ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
     lib.abea_server_submit.argtypes = [P, ctypes.POINTER(Read), ctypes.POINTER(i64)]
     lib.abea_server_poll.argtypes = [P, i64, i32, ctypes.POINTER(Result), P, i32, ctypes.POINTER(ctypes.c_double)]
@@ -211,6 +214,18 @@ class Context:
             self.h, n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
             _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
             ctypes.c_void_p(stream)), "abea_align_batch_device")
+
+    def detect_events(self, n: int, d_raw, raw_off, calib, window: int, tau2: float, d_events, event_off, d_n_events,
+                      stream=None):
+        """abea_detect_events: d_raw int16, d_events (16 bytes per event) and d_n_events int32 are torch
+        CUDA tensors; raw_off, calib (float32[n, 2]) and event_off host arrays."""
+        ro = np.ascontiguousarray(raw_off, np.int64)
+        eo = np.ascontiguousarray(event_off, np.int64)
+        ca = np.ascontiguousarray(calib, np.float32)
+        _check(self.lib.abea_detect_events(
+            self.h, n, ctypes.c_void_p(d_raw.data_ptr()), _p(ro), _p(ca), window, tau2,
+            ctypes.c_void_p(d_events.data_ptr()), _p(eo), ctypes.c_void_p(d_n_events.data_ptr()),
+            ctypes.c_void_p(stream)), "abea_detect_events")
 
     def estimate_scalings(self, n: int, d_seq, seq_off, d_events, ev_off, d_out, d_status, stream=None):
         """abea_estimate_scalings: d_* are torch CUDA tensors (uint8 bases, float32 events, float32[n*3]

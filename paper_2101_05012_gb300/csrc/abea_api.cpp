@@ -52,9 +52,9 @@ struct abea_ctx {
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
     DevBuf model;
-    DevBuf rd, order, flags, kc, trace, moves, queue, offs;
+    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ev_bnd;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
-    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs;
+    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs, h_ev_meta;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
@@ -421,9 +421,11 @@ void abea_destroy(abea_ctx *c)
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     cudaDeviceSynchronize();
     DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
-                     &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs};
+                     &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs, &c->ev_meta, &c->ev_bits,
+                     &c->ev_bnd};
     for (DevBuf *b : dev) free_dev(*b);
-    HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs};
+    HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs,
+                       &c->h_ev_meta};
     for (HostBuf *b : host) free_host(*b);
     for (cudaEvent_t e : c->wave_t0) cudaEventDestroy(e);
     for (cudaEvent_t e : c->wave_t1) cudaEventDestroy(e);
@@ -651,6 +653,60 @@ int abea_align(abea_ctx *c, const abea_read *read, int W, abea_result *out, int3
     if (rc) return rc;
     if (out->status == ABEA_READ_CAPACITY) return ABEA_ERR_CAPACITY;
     return ABEA_OK;
+}
+
+int abea_detect_events(abea_ctx *c, int32_t n, const int16_t *d_raw, const int64_t *raw_off,
+                       const abea_calib *calib, int window, float tau2, abea_event *d_events,
+                       const int64_t *event_off, int32_t *d_n_events, void *cuda_stream)
+{
+    if (!c) return ABEA_ERR_ARG;
+    if (n < 0 || window < 2 || window > 8 || !std::isfinite(tau2) || tau2 < 0.0f) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    if (!d_raw || !raw_off || !calib || !event_off || !d_n_events || (!d_events && event_off[n] > event_off[0]))
+        return ABEA_ERR_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (raw_off[i + 1] < raw_off[i] || raw_off[i + 1] - raw_off[i] > INT32_MAX / 2 ||
+            event_off[i + 1] < event_off[i] || !std::isfinite(calib[i].offset) || !std::isfinite(calib[i].pa_per_unit))
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    int rc;
+    if ((rc = order_after_previous(c, st))) return rc;
+    // per-read layout of the scratch: one bit per sample, one record per event start (at most
+    // len/window + 1 starts, plus the records at 0 and at the end)
+    const size_t m = (size_t)(n + 1);
+    const size_t meta_bytes = 4 * m * sizeof(int64_t) + (size_t)n * sizeof(abea_calib);
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    if ((rc = ensure_host(c->h_ev_meta, meta_bytes))) return rc;
+    int64_t *h_raw_off = (int64_t *)c->h_ev_meta.p, *h_ev_off = h_raw_off + m, *h_bits_off = h_ev_off + m,
+            *h_bnd_off = h_bits_off + m;
+    abea_calib *h_cal = (abea_calib *)(h_bnd_off + m);
+    h_bits_off[0] = 0;
+    h_bnd_off[0] = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const int64_t len = raw_off[i + 1] - raw_off[i];
+        h_raw_off[i] = raw_off[i] - raw_off[0];
+        h_ev_off[i] = event_off[i] - event_off[0];
+        h_bits_off[i + 1] = h_bits_off[i] + (len + 31) / 32;
+        h_bnd_off[i + 1] = h_bnd_off[i] + len / window + 3;
+        h_cal[i] = calib[i];
+    }
+    h_raw_off[n] = raw_off[n] - raw_off[0];
+    h_ev_off[n] = event_off[n] - event_off[0];
+    if ((rc = ensure_dev(c, c->ev_meta, meta_bytes, st))) return rc;
+    if ((rc = ensure_dev(c, c->ev_bits, std::max<size_t>((size_t)h_bits_off[n], 1) * 4, st))) return rc;
+    if ((rc = ensure_dev(c, c->ev_bnd, std::max<size_t>((size_t)h_bnd_off[n], 1) * abea::event_record_bytes(), st)))
+        return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->ev_meta.p, h_raw_off, meta_bytes, cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
+    const int64_t *d_meta = (const int64_t *)c->ev_meta.p;
+    if ((rc = cuda_err((cudaError_t)abea::launch_events(
+             d_meta, n, d_raw + raw_off[0], (const abea_calib *)(d_meta + 4 * m), window, tau2,
+             (uint32_t *)c->ev_bits.p, d_meta + 2 * m, c->ev_bnd.p, d_meta + 3 * m, d_events + event_off[0], d_meta + m,
+             d_n_events, st))))
+        return rc;
+    c->last_launches++;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
 }
 
 int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,
