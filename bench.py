@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--depth", type=int, default=6, help="batches in flight (one context and stream each)")
+    p.add_argument("--event-reads", type=int, default=1024, help="reads whose raw signals event detection runs on")
     p.add_argument("--serve-requests", type=int, default=500,
                    help="serve_mix requests at 1x offered load (4x as many at 10x); 0 skips serving")
     p.add_argument("--block-theta", type=float, default=0.0,
@@ -480,6 +481,40 @@ def run_ours(args):
                                   "frac": scal_bytes / (scal_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": scal_bytes},
                      "ok_reads": int((d_sst == 0).sum().item())}
 
+    # event detection over the raw signals of the first 1,024 reads (about 9 samples per base,
+    # int16): a streaming pass over the samples
+    events_line = None
+    if args.event_reads > 0:
+        rb = synth.make_raw_batch(args.workload, n_reads=min(args.event_reads, synth.WORKLOADS[args.workload].n_reads))
+        d_raw = torch.from_numpy(rb.raw).to(dev)
+        ev_cap = (rb.raw_off[1:] - rb.raw_off[:-1]) // 3 + 2
+        ev_off = np.zeros(rb.n + 1, np.int64)
+        np.cumsum(ev_cap, out=ev_off[1:])
+        d_evs = torch.zeros(int(ev_off[-1]) * 16, dtype=torch.uint8, device=dev)
+        d_nev = torch.zeros(rb.n, dtype=torch.int32, device=dev)
+
+        def detect():
+            ctxs[0].detect_events(rb.n, d_raw, rb.raw_off, rb.calib, 3, 2.0, d_evs, ev_off, d_nev,
+                                  stream=streams[0].cuda_stream)
+
+        for _ in range(3):
+            detect()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(streams[0])
+        for _ in range(args.steps):
+            detect()
+        q1.record(streams[0])
+        q1.synchronize()
+        det_ms = q0.elapsed_time(q1) / args.steps
+        n_events = int(d_nev.sum().item())
+        det_bytes = int(rb.raw.nbytes + n_events * 16)
+        events_line = {"kernel": "events_kernel<3>", "reads": rb.n, "samples": int(rb.raw.size), "events": n_events,
+                       "ms_per_launch": det_ms, "samples_per_s": rb.raw.size / (det_ms / 1e3),
+                       "roofline": {"bound": "hbm", "achieved": det_bytes / (det_ms / 1e3) / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": det_bytes / (det_ms / 1e3) / 1e9 / hbm,
+                                    "bytes_per_launch": det_bytes}}
+        del d_raw, d_evs
+
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = [serve_latency(binding, synth, local_rank, load, n_req, 1.0)
@@ -508,7 +543,7 @@ def run_ours(args):
                         "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
                         "host_threads": D},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving,
-                "scalings_estimate": scalings_line}
+                "scalings_estimate": scalings_line, "event_detection": events_line}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

@@ -90,34 +90,39 @@ __global__ void __launch_bounds__(kThreads) events_kernel(const int64_t *raw_off
     const long long a = (long long)threadIdx.x * chunk;
     const long long b = (a + chunk < n) ? a + chunk : n;
 
-    // pass 1: t2 and event starts over [a, b)
+    // pass 1: t2 and event starts over [a, b).  The samples x[p-W .. p+W] sit in a register
+    // ring (one load per step); the window sums roll in 32 bits (|S| < 2^19) and the sums of
+    // squares in 64 bits (each step adds the 32-bit difference of two squares).
     long long cnt = 0, csum = 0, csq = 0;
     if (a < b) {
         float ring[2 * W - 1];                 // t2 at p-2W+2 .. p
 #pragma unroll
         for (int r = 0; r < 2 * W - 1; r++) ring[r] = -1.0f;
+        int xs[2 * W + 1];                     // x[p-W .. p+W] (0 outside the read)
         long long p = a - (W - 1);
-        long long SL = 0, SR = 0, QL = 0, QR = 0;
-        for (int q = 1; q <= W; q++) {
-            const long long v = xg(x, p - q, n);
-            SL += v;
-            QL += v * v;
-        }
+#pragma unroll
+        for (int q = 0; q < 2 * W + 1; q++) xs[q] = xg(x, p - W + q, n);
+        int SL = 0, SR = 0;
+        long long QL = 0, QR = 0;
+#pragma unroll
         for (int q = 0; q < W; q++) {
-            const long long v = xg(x, p + q, n);
-            SR += v;
-            QR += v * v;
+            SL += xs[q];
+            QL += xs[q] * xs[q];
+            SR += xs[W + q];
+            QR += xs[W + q] * xs[W + q];
         }
         uint32_t word = 0;
+        int ccount = 0;
+        long long cs = 0;
         const long long p_end = b + W - 1;
         for (; p < p_end; p++) {
             float t2 = -1.0f;                  // outside the read
             if (p >= 0 && p < n) {
                 t2 = 0.0f;
                 if (p >= W && p <= n - W) {
-                    const long long d = SR - SL;
-                    const long long N = (long long)W * d * d;
-                    const long long D = (long long)W * (QL + QR) - SL * SL - SR * SR;
+                    const int d = SR - SL;
+                    const long long N = (long long)W * ((long long)d * d);
+                    const long long D = (long long)W * (QL + QR) - (long long)SL * SL - (long long)SR * SR;
                     if (D == 0) t2 = (N > 0) ? __int_as_float(0x7f800000) : 0.0f;
                     else t2 = __fdiv_rn(__ll2float_rn(N), __ll2float_rn(D));
                 }
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) events_kernel(const int64_t *raw_off
             for (int r = 0; r < 2 * W - 2; r++) ring[r] = ring[r + 1];
             ring[2 * W - 2] = t2;
             const long long c = p - (W - 1);   // ring[W-1] holds t2_c
-            if (c >= a && c < b) {
+            if (c >= a) {                      // c < b holds for every p < p_end
                 const float v = ring[W - 1];
                 bool start = (c >= 1) && (v >= tau2);
 #pragma unroll
@@ -135,23 +140,28 @@ __global__ void __launch_bounds__(kThreads) events_kernel(const int64_t *raw_off
                 for (int r = W; r < 2 * W - 1; r++) start = start && !(ring[r] > v);
                 const int bit = (int)((c - a) & 31);
                 word |= (start ? 1u : 0u) << bit;
-                cnt += start ? 1 : 0;
-                const long long xv = x[c];
-                csum += xv;
+                ccount += start ? 1 : 0;
+                const int xv = xs[1];          // x[c] = x[p-W+1]
+                cs += xv;
                 csq += xv * xv;
                 if (bit == 31 || c == b - 1) {
                     bw[c >> 5] = word;
                     word = 0;
                 }
             }
-            // roll the windows to p+1
-            const long long in_l = xg(x, p, n), out_l = xg(x, p - W, n);
-            const long long in_r = xg(x, p + W, n), out_r = in_l;
-            SL += in_l - out_l;
-            QL += in_l * in_l - out_l * out_l;
-            SR += in_r - out_r;
-            QR += in_r * in_r - out_r * out_r;
+            // roll to p+1: x[p] leaves the right window for the left, x[p-W] leaves, x[p+W] enters
+            const int in_r = xg(x, p + W + 1, n);
+            const int x_p = xs[W], out_l = xs[0], new_r = xs[2 * W];
+            SL += x_p - out_l;
+            QL += x_p * x_p - out_l * out_l;
+            SR += new_r - x_p;
+            QR += new_r * new_r - x_p * x_p;
+#pragma unroll
+            for (int q = 0; q < 2 * W; q++) xs[q] = xs[q + 1];
+            xs[2 * W] = in_r;
         }
+        cnt = ccount;
+        csum = cs;
     }
     long long tot[3];
     block_scan3(cnt, csum, csq, tot, sh);      // cnt, csum, csq become this chunk's exclusive prefixes
@@ -164,11 +174,15 @@ __global__ void __launch_bounds__(kThreads) events_kernel(const int64_t *raw_off
     }
     if (a < b) {
         long long e = cnt + 1, S = csum, Q = csq;
-        for (long long c = a; c < b; c++) {
-            if ((bw[c >> 5] >> (c & 31)) & 1u) rec[e++] = Bound{S, Q, (int)c, 0};
-            const long long xv = x[c];
-            S += xv;
-            Q += xv * xv;
+        for (long long c0 = a; c0 < b; c0 += 32) {
+            uint32_t word = bw[c0 >> 5];
+            const int m = (b - c0 < 32) ? (int)(b - c0) : 32;
+            for (int j = 0; j < m; j++) {
+                if ((word >> j) & 1u) rec[e++] = Bound{S, Q, (int)(c0 + j), 0};
+                const int xv = x[c0 + j];
+                S += xv;
+                Q += xv * xv;
+            }
         }
     }
     __syncthreads();
