@@ -287,3 +287,22 @@ def test_wide_k9_w200_sample(ctx):
     res, pairs, po = run_gpu(ctx, b)
     assert np.all(res["status"] == 0)
     compare(b, res, pairs, po)
+
+
+def test_large_workload_sample_with_ultra_long_reads(ctx):
+    """Reads of the 50,000-read workload, the three longest (about 200 kb, half a
+    million bands) among them, in one launch and then in memory-budget waves;
+    every read against the FP32 oracle."""
+    w = synth.WORKLOADS["large_50k_ln8kb"]
+    L = synth.read_lengths(w)
+    ids = sorted(set(np.argsort(-L)[:3].tolist()) | set(range(0, w.n_reads, w.n_reads // 12)))
+    b = synth.make_batch(w, read_ids=ids)
+    res, pairs, po = run_gpu(ctx, b)
+    assert np.all(res["status"] == 0)
+    compare(b, res, pairs, po, check_f64=False)
+    # the same reads under a budget that forces several waves (the longest read alone needs ~40 MB)
+    with binding.Context(0, mem_budget_bytes=64 << 20) as small:
+        r2, p2, po2 = run_gpu(small, b)
+        launches, _ = small.last_launch_stats()
+    assert launches >= 4
+    assert np.array_equal(res, r2) and np.array_equal(pairs, p2)
