@@ -450,7 +450,7 @@ int abea_set_model(abea_ctx *c, int k, const float *level_mean, const float *lev
         m[r].mu = (double)mu;
         m[r].a0 = kSqrtHalf / (double)sd;
         m[r].c0 = kLogInvSqrt2Pi - std::log((double)sd);
-        m[r].pad = 0.0;
+        m[r].sd = (double)sd;
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
     if (cudaStreamSynchronize(c->own_stream) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)

@@ -28,12 +28,12 @@ struct ReadDesc {
 };
 static_assert(sizeof(ReadDesc) == 112, "descriptor layout");
 
-// Per model row: mean, sqrt(1/2)/stdv and ln(1/sqrt(2 pi)) - ln(stdv), FP64.
+// Per model row: mean, sqrt(1/2)/stdv, ln(1/sqrt(2 pi)) - ln(stdv) and stdv, FP64.
 struct ModelRow {
     double mu;
     double a0;
     double c0;
-    double pad;
+    double sd;          // the stdv as given
 };
 
 // Band-record geometry for a band width W: C offsets per lane, L lanes,

@@ -129,7 +129,7 @@ extern "C" int abea_align_batch_device_noalloc(int k, const float *level_mean, c
         s_rows[r].mu = (double)mu;
         s_rows[r].a0 = kSqrtHalf / (double)sd;
         s_rows[r].c0 = kLogInvSqrt2Pi - std::log((double)sd);
-        s_rows[r].pad = 0.0;
+        s_rows[r].sd = (double)sd;
     }
     size_t ckc = 0, ctr = 0, cmv = 0;
     for (int32_t i = 0; i < n; i++) {

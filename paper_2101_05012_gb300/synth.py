@@ -32,7 +32,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream tags
 _T_LEN, _T_ULTRA, _T_SEQ, _T_SKIP, _T_DWELL, _T_NOISE, _T_SCALE, _T_MODEL, _T_ARRIVAL, _T_CLASS = range(1, 11)
-_T_RAW_DWELL, _T_RAW_NOISE, _T_CALIB = range(11, 14)
+_T_RAW_DWELL, _T_RAW_NOISE, _T_CALIB, _T_REF = range(11, 15)
 
 BASES = np.frombuffer(b"ACGT", dtype=np.uint8)
 
@@ -402,4 +402,33 @@ def make_raw_batch(w, n_reads: Optional[int] = None, read_ids=None) -> RawBatch:
     return RawBatch(w.k, mm, ms, np.concatenate(seqs), _offsets([len(x) for x in seqs]),
                     np.concatenate(raws), _offsets([len(x) for x in raws]), np.stack(cals),
                     np.concatenate(sts), _offsets([len(x) for x in sts]), w.name)
+
+
+def make_ref_alignment(seq, seed: int, r: int, indel_rate: float = 0.03):
+    """A reference around a read and the read's base-space alignment to it.
+
+    The reference is the read's bases with indels: at each read base, with
+    probability indel_rate/2 the base is missing from the reference (the read
+    base is an insertion, aligned to no reference position) and with
+    probability indel_rate/2 one random base is inserted into the reference
+    before it.  Returns (ref bytes, ref_pos int32[len(seq)]): the reference
+    position of each read base, -1 for inserted read bases.
+    """
+    s = np.frombuffer(seq.encode() if isinstance(seq, str) else bytes(seq), np.uint8)
+    n = len(s)
+    u = draw_unit(stream_key(seed, _T_REF, r), np.arange(2 * n, dtype=np.uint64))
+    drop = u[:n] < indel_rate / 2
+    ins = (u[:n] >= indel_rate / 2) & (u[:n] < indel_rate)
+    extra = BASES[(draw_u64(stream_key(seed, _T_REF, r), np.arange(2 * n, 3 * n, dtype=np.uint64))
+                   & np.uint64(3)).astype(np.int64)]
+    ref = []
+    pos = np.full(n, -1, np.int32)
+    for i in range(n):
+        if ins[i]:
+            ref.append(extra[i])
+        if drop[i]:
+            continue
+        pos[i] = len(ref)
+        ref.append(s[i])
+    return np.array(ref, dtype=np.uint8), pos
 
