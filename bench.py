@@ -481,6 +481,41 @@ def run_ours(args):
                                   "frac": scal_bytes / (scal_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": scal_bytes},
                      "ok_reads": int((d_sst == 0).sum().item())}
 
+    # eventalign rows over the batch's alignments (context 0's results and pairs), each read mapped to a
+    # reference with 3 % indels: a gather pass, 8 B of pair + 4 B of event + 4 B of reference position in,
+    # 40 B of record out per pair
+    ea_refs, ea_pos, ea_base = [], np.zeros(len(batch.seq), np.int32), 0
+    for i in range(n):
+        r_, p_ = synth.make_ref_alignment(batch.seq[batch.seq_off[i]:batch.seq_off[i + 1]].tobytes(), 9, i)
+        ea_pos[batch.seq_off[i]:batch.seq_off[i + 1]] = np.where(p_ >= 0, p_ + ea_base, -1)
+        ea_refs.append(r_)
+        ea_base += len(r_)
+    d_ref = torch.from_numpy(np.concatenate(ea_refs)).to(dev)
+    d_rpos = torch.from_numpy(ea_pos).to(dev)
+    d_rows = torch.empty(n_pairs * 40, dtype=torch.uint8, device=dev)
+
+    def eventalign():
+        ctxs[0].eventalign(n, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out[0], d_pairs[0],
+                           pair_off, d_rpos, d_ref, ea_base, False, d_rows, stream=streams[0].cuda_stream)
+
+    for _ in range(3):
+        eventalign()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(streams[0])
+    for _ in range(args.steps):
+        eventalign()
+    a1.record(streams[0])
+    a1.synchronize()
+    ea_ms = a0.elapsed_time(a1) / args.steps
+    rows_n = int(res["n_pairs"].sum())
+    ea_bytes = rows_n * (8 + 4 + 4 + 40)
+    eventalign_line = {"kernel": "eventalign_kernel", "rows": rows_n, "ms_per_launch": ea_ms,
+                       "rows_per_s": rows_n / (ea_ms / 1e3),
+                       "roofline": {"bound": "hbm", "achieved": ea_bytes / (ea_ms / 1e3) / 1e9, "peak": hbm,
+                                    "unit": "GB/s", "frac": ea_bytes / (ea_ms / 1e3) / 1e9 / hbm,
+                                    "bytes_per_launch": ea_bytes}}
+    del d_ref, d_rpos, d_rows
+
     # event detection over the raw signals of the first 1,024 reads (about 9 samples per base,
     # int16): a streaming pass over the samples
     events_line = None
@@ -543,7 +578,7 @@ def run_ours(args):
                         "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
                         "host_threads": D},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving,
-                "scalings_estimate": scalings_line, "event_detection": events_line}
+                "scalings_estimate": scalings_line, "event_detection": events_line, "eventalign": eventalign_line}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

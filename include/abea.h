@@ -153,6 +153,31 @@ int abea_align_batch_device(abea_ctx *ctx, int32_t n, int W,
  * between two calls (later ones are folded into the last slot). */
 int abea_last_launch_stats(abea_ctx *ctx, int32_t *n_launches, float *align_kernel_ms);
 
+/* eventalign rows (f5c's eventalign: events aligned to reference k-mers; the
+ * thesis gives no record format).  For every read i with d_results[i].status
+ * == ABEA_READ_OK, its d_results[i].n_pairs pairs (event e, read k-mer j) at
+ * d_pairs + 2*pair_off[i] become records d_rows[pair_off[i] + t]:
+ *   ref_pos    reference position of k-mer j's first base, d_ref_pos[seq_off[i] + j]
+ *              (the read's base-space alignment: one int32 per read base, -1 for an insertion),
+ *   ref_rank   rank of d_ref[ref_pos .. ref_pos+k) (-1 if unaligned, past ref_len or not ACGT),
+ *   model_rank rank of the read k-mer,
+ *   default:       level = x_e, model_mean = mu*scale + shift, model_stdv = sigma*var;
+ *   scale_events:  level = (x_e - shift)/scale, model_mean = mu, model_stdv = sigma*var/scale;
+ *   z = (level - model_mean) / model_stdv (FP32, one operation at a time in that order).
+ * Rows of other reads and past n_pairs are not written.  d_* are device
+ * pointers (d_seq, d_events, d_results, d_pairs as given to and returned by
+ * abea_align_batch_device), seq_off, ev_off, sc and pair_off host arrays;
+ * uses ctx's model; enqueued on cuda_stream. */
+typedef struct {
+    int32_t read, event, kmer, ref_pos, ref_rank, model_rank;
+    float level, model_mean, model_stdv, z;
+} abea_eventalign_row;
+int abea_eventalign(abea_ctx *ctx, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,
+                    const float *d_events, const int64_t *ev_off, const abea_scalings *sc,
+                    const abea_result *d_results, const int32_t *d_pairs, const int64_t *pair_off,
+                    const int32_t *d_ref_pos, const uint8_t *d_ref, int64_t ref_len, int scale_events,
+                    abea_eventalign_row *d_rows, void *cuda_stream);
+
 /* Event detection: raw signal -> events (thesis Sec. "Methylation calling":
  * the raw signal is segmented at sudden level changes, each segment an event
  * with the mean, standard deviation and duration of its samples; the thesis

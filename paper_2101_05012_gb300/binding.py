@@ -29,7 +29,7 @@ SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 # the functions include/abea.h declares
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
-           "abea_set_block_mode", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
+           "abea_set_block_mode", "abea_eventalign", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
            "abea_server_stop", "abea_align_batch_device_noalloc"]
 
 
@@ -52,6 +52,10 @@ class Result(ctypes.Structure):
     _fields_ = [("score", ctypes.c_float), ("status", ctypes.c_int32), ("n_pairs", ctypes.c_int32),
                 ("e_end", ctypes.c_int32), ("cells", ctypes.c_int64)]
 
+
+EVENTALIGN_DTYPE = np.dtype([("read", "<i4"), ("event", "<i4"), ("kmer", "<i4"), ("ref_pos", "<i4"),
+                             ("ref_rank", "<i4"), ("model_rank", "<i4"), ("level", "<f4"), ("model_mean", "<f4"),
+                             ("model_stdv", "<f4"), ("z", "<f4")])
 
 EVENT_DTYPE = np.dtype([("mean", "<f4"), ("stdv", "<f4"), ("start", "<i4"), ("length", "<i4")])
 
@@ -95,6 +99,7 @@ def load(path: Optional[str] = None):
     lib.abea_set_block_mode.argtypes = [P, ctypes.c_double]
     lib.abea_estimate_scalings.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.abea_detect_events.argtypes = [P, i32, P, P, P, ctypes.c_int, ctypes.c_float, P, P, P, P]
+    lib.abea_eventalign.argtypes = [P, i32, P, P, P, P, P, P, P, P, P, P, i64, ctypes.c_int, P, P]
     lib.abea_server_start.argtypes = [P, ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
     lib.abea_server_submit.argtypes = [P, ctypes.POINTER(Read), ctypes.POINTER(i64)]
     lib.abea_server_poll.argtypes = [P, i64, i32, ctypes.POINTER(Result), P, i32, ctypes.POINTER(ctypes.c_double)]
@@ -214,6 +219,21 @@ class Context:
             self.h, n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo),
             _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
             ctypes.c_void_p(stream)), "abea_align_batch_device")
+
+    def eventalign(self, n: int, d_seq, seq_off, d_events, ev_off, scalings, d_results, d_pairs, pair_off, d_ref_pos,
+                   d_ref, ref_len: int, scale_events: bool, d_rows, stream=None):
+        """abea_eventalign: d_* are torch CUDA tensors (d_results and d_pairs as filled by
+        align_batch_device, d_rows 40 bytes per pair slot); offsets and scalings host arrays."""
+        so = np.ascontiguousarray(seq_off, np.int64)
+        eo = np.ascontiguousarray(ev_off, np.int64)
+        po = np.ascontiguousarray(pair_off, np.int64)
+        sc = np.ascontiguousarray(scalings, np.float32)
+        _check(self.lib.abea_eventalign(
+            self.h, n, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()), _p(eo), _p(sc),
+            ctypes.c_void_p(d_results.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
+            ctypes.c_void_p(d_ref_pos.data_ptr()), ctypes.c_void_p(d_ref.data_ptr()), int(ref_len),
+            1 if scale_events else 0, ctypes.c_void_p(d_rows.data_ptr()), ctypes.c_void_p(stream)),
+            "abea_eventalign")
 
     def detect_events(self, n: int, d_raw, raw_off, calib, window: int, tau2: float, d_events, event_off, d_n_events,
                       stream=None):

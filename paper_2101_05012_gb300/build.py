@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libabea.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["abea_align.cu", "abea_prep.cu", "abea_api.cpp", "abea_noalloc.cu", "abea_server.cpp", "abea_scalings.cu", "abea_events.cu"]
+SOURCES = ["abea_align.cu", "abea_prep.cu", "abea_api.cpp", "abea_noalloc.cu", "abea_server.cpp", "abea_scalings.cu", "abea_events.cu", "abea_eventalign.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -52,9 +52,9 @@ struct abea_ctx {
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
     DevBuf model;
-    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ev_bnd;
+    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ev_bnd, ea_meta;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
-    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs, h_ev_meta;
+    HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs, h_ev_meta, h_ea_meta;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
     std::vector<cudaEvent_t> wave_t0, wave_t1;   // one pair per timed core-kernel launch
     int32_t n_timed = 0;                        // pairs recorded since the last stats call
@@ -422,10 +422,10 @@ void abea_destroy(abea_ctx *c)
     cudaDeviceSynchronize();
     DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
                      &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs, &c->ev_meta, &c->ev_bits,
-                     &c->ev_bnd};
+                     &c->ev_bnd, &c->ea_meta};
     for (DevBuf *b : dev) free_dev(*b);
     HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs,
-                       &c->h_ev_meta};
+                       &c->h_ev_meta, &c->h_ea_meta};
     for (HostBuf *b : host) free_host(*b);
     for (cudaEvent_t e : c->wave_t0) cudaEventDestroy(e);
     for (cudaEvent_t e : c->wave_t1) cudaEventDestroy(e);
@@ -653,6 +653,47 @@ int abea_align(abea_ctx *c, const abea_read *read, int W, abea_result *out, int3
     if (rc) return rc;
     if (out->status == ABEA_READ_CAPACITY) return ABEA_ERR_CAPACITY;
     return ABEA_OK;
+}
+
+int abea_eventalign(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t *seq_off, const float *d_events,
+                    const int64_t *ev_off, const abea_scalings *sc, const abea_result *d_results,
+                    const int32_t *d_pairs, const int64_t *pair_off, const int32_t *d_ref_pos, const uint8_t *d_ref,
+                    int64_t ref_len, int scale_events, abea_eventalign_row *d_rows, void *cuda_stream)
+{
+    if (!c) return ABEA_ERR_ARG;
+    if (c->k <= 0) return ABEA_ERR_NO_MODEL;
+    if (n < 0 || ref_len < 0) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    if (!d_seq || !seq_off || !d_events || !ev_off || !sc || !d_results || !d_pairs || !pair_off || !d_ref_pos ||
+        (!d_ref && ref_len > 0) || !d_rows)
+        return ABEA_ERR_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (seq_off[i + 1] < seq_off[i] || ev_off[i + 1] < ev_off[i] || pair_off[i + 1] < pair_off[i] ||
+            !(sc[i].scale != 0.0f) || !std::isfinite(sc[i].scale))
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    int rc;
+    if ((rc = order_after_previous(c, st))) return rc;
+    const size_t m = (size_t)(n + 1);
+    const size_t bytes = 3 * m * sizeof(int64_t) + (size_t)n * sizeof(abea_scalings);
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    if ((rc = ensure_host(c->h_ea_meta, bytes))) return rc;
+    int64_t *h = (int64_t *)c->h_ea_meta.p;
+    std::memcpy(h, seq_off, m * sizeof(int64_t));
+    std::memcpy(h + m, ev_off, m * sizeof(int64_t));
+    std::memcpy(h + 2 * m, pair_off, m * sizeof(int64_t));
+    std::memcpy(h + 3 * m, sc, (size_t)n * sizeof(abea_scalings));
+    if ((rc = ensure_dev(c, c->ea_meta, bytes, st))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->ea_meta.p, h, bytes, cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
+    const int64_t *d_meta = (const int64_t *)c->ea_meta.p;
+    if ((rc = cuda_err((cudaError_t)abea::launch_eventalign(
+             d_meta, n, d_seq, d_events, (const abea_scalings *)(d_meta + 3 * m), d_results, d_pairs, d_ref_pos, d_ref,
+             ref_len, (const ModelRow *)c->model.p, c->k, scale_events ? 1 : 0, d_rows, st))))
+        return rc;
+    c->last_launches++;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
 }
 
 int abea_detect_events(abea_ctx *c, int32_t n, const int16_t *d_raw, const int64_t *raw_off,

@@ -69,6 +69,10 @@ struct AlignArgs {
 int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *events,
                 const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
 int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream);
+int launch_eventalign(const int64_t *meta, int32_t n, const uint8_t *seq, const float *events,
+                      const abea_scalings *sc, const abea_result *res, const int32_t *pairs, const int32_t *ref_pos,
+                      const uint8_t *ref, int64_t ref_len, const ModelRow *model, int k, int scale_events,
+                      abea_eventalign_row *rows, void *stream);
 int launch_events(const int64_t *raw_off, int32_t n, const int16_t *raw, const abea_calib *calib, int window,
                   float tau2, uint32_t *bits, const int64_t *bits_off, void *bnd, const int64_t *bnd_off,
                   abea_event *out, const int64_t *ev_off, int32_t *n_ev, void *stream);

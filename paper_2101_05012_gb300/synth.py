@@ -421,14 +421,12 @@ def make_ref_alignment(seq, seed: int, r: int, indel_rate: float = 0.03):
     ins = (u[:n] >= indel_rate / 2) & (u[:n] < indel_rate)
     extra = BASES[(draw_u64(stream_key(seed, _T_REF, r), np.arange(2 * n, 3 * n, dtype=np.uint64))
                    & np.uint64(3)).astype(np.int64)]
-    ref = []
-    pos = np.full(n, -1, np.int32)
-    for i in range(n):
-        if ins[i]:
-            ref.append(extra[i])
-        if drop[i]:
-            continue
-        pos[i] = len(ref)
-        ref.append(s[i])
-    return np.array(ref, dtype=np.uint8), pos
+    ins_n = ins.astype(np.int64)
+    keep = (~drop).astype(np.int64)
+    start = np.concatenate([[0], np.cumsum(ins_n + keep)[:-1]])     # reference index of read base i's slot
+    ref = np.zeros(int((ins_n + keep).sum()), np.uint8)
+    ref[start[ins]] = extra[ins]
+    pos = np.where(drop, -1, start + ins_n).astype(np.int32)
+    ref[pos[~drop]] = s[~drop]
+    return ref, pos
 

@@ -1,0 +1,68 @@
+"""GPU eventalign rows (abea_eventalign) against the oracle, from ABEA's own
+device outputs: every field identical, in both level modes; reads that did
+not align produce no rows."""
+import numpy as np
+import pytest
+
+from oracle import eventalign_oracle as ea
+from paper_2101_05012_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rows_match_the_oracle():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    b0 = synth.make_batch("plain_64x1kb", n_reads=24)
+    # one read with a bad base: ABEA rejects it, eventalign writes nothing for it
+    evs, sqs, scs = zip(*[b0.read(i) for i in range(b0.n)])
+    sqs = list(sqs)
+    sqs[5] = sqs[5][:100] + b"N" + sqs[5][101:]
+    b = synth.custom_batch(list(evs), sqs, list(scs), b0.model_mean, b0.model_stdv, b0.k, b0.W)
+    # one reference holding every read's reference, with per-base positions into it
+    refs, pos = [], np.zeros(len(b.seq), np.int32)
+    base = 0
+    for i in range(b.n):
+        r, p = synth.make_ref_alignment(b.seq[b.seq_off[i]:b.seq_off[i + 1]].tobytes(), 9, i)
+        pos[b.seq_off[i]:b.seq_off[i + 1]] = np.where(p >= 0, p + base, -1)
+        refs.append(r)
+        base += len(r)
+    ref = np.concatenate(refs)
+    po = binding.pair_offsets(b.n_events(), np.maximum(b.n_kmers(), 1))
+    with binding.Context(0) as ctx:
+        ctx.set_model(b.k, b.model_mean, b.model_stdv)
+        d_seq = torch.from_numpy(b.seq).to(dev)
+        d_ev = torch.from_numpy(b.events).to(dev)
+        d_res = torch.zeros(b.n * 24, dtype=torch.uint8, device=dev)
+        d_pairs = torch.zeros(int(po[-1]) * 2, dtype=torch.int32, device=dev)
+        d_pos = torch.from_numpy(pos).to(dev)
+        d_ref = torch.from_numpy(ref).to(dev)
+        s = torch.cuda.Stream(dev)
+        ctx.align_batch_device(b.n, b.W, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_res, d_pairs, po,
+                               stream=s.cuda_stream)
+        out = {}
+        for mode in (False, True):
+            d_rows = torch.zeros(int(po[-1]) * 40, dtype=torch.uint8, device=dev)
+            ctx.eventalign(b.n, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_res, d_pairs, po, d_pos, d_ref,
+                           len(ref), mode, d_rows, stream=s.cuda_stream)
+            s.synchronize()
+            out[mode] = np.frombuffer(d_rows.cpu().numpy().tobytes(), binding.EVENTALIGN_DTYPE)
+        res = binding.results_from_bytes(d_res.cpu().numpy())
+        pairs = d_pairs.cpu().numpy().reshape(-1, 2)
+    assert res["status"][5] == binding.READ_BAD_INPUT and np.sum(res["status"] == 0) == b.n - 1
+    for mode in (False, True):
+        rows = out[mode]
+        for i in range(b.n):
+            got = rows[po[i]:po[i + 1]]
+            if res["status"][i] != 0:
+                assert np.all(got["read"] == 0) and np.all(got["z"] == 0)    # untouched
+                continue
+            n = int(res["n_pairs"][i])
+            e, sq, sc = b.read(i)
+            want = ea.rows(i, b.model_mean, b.model_stdv, b.k, sq, e, sc, pairs[po[i]:po[i] + n], ref,
+                           pos[b.seq_off[i]:b.seq_off[i + 1]], scale_events=mode)
+            g = got[:n]
+            for f in binding.EVENTALIGN_DTYPE.names:
+                assert np.array_equal(g[f], want[f]), (mode, i, f)
+    # the reference positions of the k-mers are shifted by the read's indels, and some bases are insertions
+    assert np.any(out[False]["ref_pos"] < 0)
