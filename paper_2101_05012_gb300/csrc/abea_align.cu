@@ -1102,8 +1102,17 @@ struct Smem {
 // Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
 // n_group-1] in block mode (CG offsets per lane); then every warp takes reads
 // order[n_group ..] one at a time from the shared counter.
+// Blocks per SM the register budget is set for: 5 where the band fits in at
+// most 96 registers without spilling much (C <= 2, and C = 4 with 25 lanes:
+// measured 3 % faster than 4 blocks at W = 100), 4 for the rest up to C = 5,
+// 3 for C >= 6 (168 registers; 10 % faster than 2 blocks at W = 200).
+template <int C, bool MIXED, bool FULLW>
+struct Occupancy {
+    static constexpr int blocks = (C >= 6) ? 3 : (C <= 2 || (C == 4 && !MIXED && !FULLW)) ? 5 : 4;
+};
+
 template <int C, bool MIXED, bool FULLW, int CG>
-__global__ void __launch_bounds__(kWarps * 32, (C >= 6) ? 2 : 4) align_kernel(const AlignArgs a)
+__global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::blocks) align_kernel(const AlignArgs a)
 {
     constexpr int RB = Smem<C, CG>::RB;
     const int lane = threadIdx.x & 31;
