@@ -34,7 +34,8 @@
 //     or two bands, selected by the last two moves; the four cases are
 //     compiled separately so every register index is static;
 //   - the move of band b+1 is decided at the end of band b (two shuffles of
-//     its end cells), so the decision overlaps band b's bookkeeping;
+//     its end cells and a vote), so the decision overlaps band b's
+//     bookkeeping;
 //   - the direction of every cell is two predicates (U over D; L over the
 //     max), gathered by __ballot_sync into 2C words per band and stored by
 //     lane 0 (2 bits per cell); the band's move rides in bit 31 of its first
@@ -497,12 +498,11 @@ __device__ __forceinline__ int lean_run(const Lane<C> &s, const ReadCtx &r)
 
 // One band of the lean loop (band b-1 and band b lie wholly in the matrix
 // and miss the end column), with the move known at compile time.  The move of
-// band b+1 needs S_b at offsets 0 and W-1.  Those two cells have no
-// neighbour across a lane edge (the lane below offset 0 and the lane above
-// offset W-1 lie outside the band), so they are formed from the lane's own
-// registers and the injected operand, and their shuffles are issued before
-// the rest of the band; the same values come out of the full band, so the
-// decision is unchanged.
+// band b+1 is decided from S_b at offsets 0 and W-1 once the whole band is
+// formed.  (Forming those two cells ahead of the band, from the lane's own
+// registers, shortens one band's critical path but adds two cells' work to
+// every lane; with four or five resident blocks per SM the extra issue slots
+// cost more than the latency they hide.)
 template <int C, bool MIXED, bool FULLW, bool KM, bool KP, bool GROUP>
 __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
 {
@@ -521,36 +521,6 @@ __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&
         s.b = b + 1;
         return;
     }
-    float lo_src, hi_src;
-    if (!MIXED) {
-        const float lp_step = r.cs.lp_step, lp_stay = r.cs.lp_stay, lsk = r.lsk;
-        // offset 0 (lane 0, slot 0)
-        {
-            const float x = KM ? s.X[0] : s.xin;
-            const float a = KM ? s.A[C > 1 ? 1 : 0] : s.A[0];
-            const float bb = KM ? s.B[C > 1 ? 1 : 0] : s.B[0];
-            const float c = KM ? s.Cc[C > 1 ? 1 : 0] : s.Cc[0];
-            const float up = KM ? P[C > 1 ? 1 : 0] : P[0];
-            const float left = KM ? P[0] : neg_inf();
-            const int t = KM ? 1 : 0;
-            const float diag = KP ? (t == C ? s.qprev : PP[t < C ? t : 0]) : (t == 0 ? s.qprev : PP[t > 0 ? t - 1 : 0]);
-            bool q0, q1;
-            lo_src = (KM && C == 1) ? 0.0f : cell(up, left, diag, x, a, bb, c, lp_step, lp_stay, lsk, q0, q1);
-        }
-        // offset W-1 (lane L-1, slot C-1)
-        {
-            const float x = KM ? s.X[C - 1] : s.X[C > 1 ? C - 2 : 0];
-            const float a = KM ? s.kin.x : s.A[C - 1];
-            const float bb = KM ? s.kin.y : s.B[C - 1];
-            const float c = KM ? s.kin.z : s.Cc[C - 1];
-            const float up = KM ? neg_inf() : P[C - 1];
-            const float left = KM ? P[C - 1] : P[C > 1 ? C - 2 : 0];
-            const int t = C - 1 + (KM ? 1 : 0);
-            const float diag = KP ? (t == C ? s.qprev : PP[t < C ? t : 0]) : (t == 0 ? s.qprev : PP[t > 0 ? t - 1 : 0]);
-            bool q0, q1;
-            hi_src = (!KM && C == 1) ? 0.0f : cell(up, left, diag, x, a, bb, c, lp_step, lp_stay, lsk, q0, q1);
-        }
-    }
     uint32_t w[2 * C];
     band_fill<C, KM, KP, FULLW, false>(s, r, P, PP, w);
     if (MIXED) {
@@ -558,16 +528,10 @@ __device__ __forceinline__ void lean_band(Lane<C> &s, const ReadCtx &r, float (&
         for (int i = 0; i < C; i++)
             if (r.dead_mask & (1u << i)) PP[i] = neg_inf();
     }
-    if (MIXED || C == 1) {
-        lo_src = PP[0];
-        hi_src = PP[C - 1];
-    }
     if (KM) s.ll_k++;
     else s.ll_e++;
-    float lo = __shfl_sync(kFull, lo_src, 0);
-    float hi;
-    if (MIXED) hi = far_end<C, MIXED>(r, PP);
-    else hi = __shfl_sync(kFull, hi_src, r.L - 1);
+    const float lo = __shfl_sync(kFull, PP[0], 0);
+    const float hi = far_end<C, MIXED>(r, PP);
     s.knext = __all_sync(kFull, lo < hi);
     store_record<C>(r, b, w);
     if (FULLW && r.lane == 0) r.mv[b] = KM ? 1 : 0;
