@@ -203,6 +203,14 @@ int abea_detect_events(abea_ctx *ctx, int32_t n, const int16_t *d_raw, const int
                        const abea_calib *calib, int window, float tau2, abea_event *d_events,
                        const int64_t *event_off, int32_t *d_n_events, void *cuda_stream);
 
+/* The integer-to-float rounding that event detection uses for its sums and
+ * t2 terms: d_out[j] = the float nearest to d_in[j], ties to even
+ * (|d_in[j]| < 2^63), formed from integer operations.  Exposed so that it can
+ * be checked against the platform's own conversion.  d_in (int64[n]) and
+ * d_out (float[n]) are device pointers; enqueued on cuda_stream.  Returns
+ * ABEA_ERR_ARG for n < 0 or a null pointer with n > 0. */
+int abea_f32_from_i64(const int64_t *d_in, int64_t n, float *d_out, void *cuda_stream);
+
 /* Per-read scalings by the method of moments (thesis Sec. "Read-model
  * scaling": shift and scale are estimated per read before ABEA, which then
  * uses mu * scale + shift; the thesis gives no formula).  For read i, with

@@ -30,7 +30,7 @@ SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
            "abea_set_block_mode", "abea_eventalign", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
-           "abea_server_stop", "abea_align_batch_device_noalloc"]
+           "abea_server_stop", "abea_align_batch_device_noalloc", "abea_f32_from_i64"]
 
 
 class Scalings(ctypes.Structure):
@@ -339,6 +339,13 @@ def align_batch_device_noalloc(k: int, level_mean, level_stdv, n: int, W: int, d
         k, _p(mm), _p(ms), n, W, ctypes.c_void_p(d_seq.data_ptr()), _p(so), ctypes.c_void_p(d_events.data_ptr()),
         _p(eo), _p(sc), ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_pairs.data_ptr()), _p(po),
         ctypes.c_void_p(stream)), "abea_align_batch_device_noalloc")
+
+
+def f32_from_i64(d_in, d_out, stream=None):
+    """abea_f32_from_i64: d_in int64 and d_out float32 torch CUDA tensors of the same length."""
+    lib = load()
+    _check(lib.abea_f32_from_i64(ctypes.c_void_p(d_in.data_ptr()), ctypes.c_int64(d_in.numel()),
+                                 ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(stream)), "abea_f32_from_i64")
 
 
 def results_from_bytes(buf: np.ndarray) -> np.ndarray:

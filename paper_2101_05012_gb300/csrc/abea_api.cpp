@@ -52,7 +52,7 @@ struct abea_ctx {
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
     DevBuf model;
-    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ev_bnd, ea_meta;
+    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ea_meta;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
     HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs, h_ev_meta, h_ea_meta;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
@@ -422,7 +422,7 @@ void abea_destroy(abea_ctx *c)
     cudaDeviceSynchronize();
     DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
                      &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs, &c->ev_meta, &c->ev_bits,
-                     &c->ev_bnd, &c->ea_meta};
+                     &c->ea_meta};
     for (DevBuf *b : dev) free_dev(*b);
     HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs,
                        &c->h_ev_meta, &c->h_ea_meta};
@@ -713,41 +713,49 @@ int abea_detect_events(abea_ctx *c, int32_t n, const int16_t *d_raw, const int64
     cudaStream_t st = pick_stream(c, cuda_stream);
     int rc;
     if ((rc = order_after_previous(c, st))) return rc;
-    // per-read layout of the scratch: one bit per sample, one record per event start (at most
-    // len/window + 1 starts, plus the records at 0 and at the end)
+    // the reads' positions in tiles of kEventTile (ceil(len / kEventTile) per read); the metadata
+    // holds the offsets of samples, events and tiles, the calibrations and each tile's read
     const size_t m = (size_t)(n + 1);
-    const size_t meta_bytes = 4 * m * sizeof(int64_t) + (size_t)n * sizeof(abea_calib);
+    int64_t n_tiles = 0;
+    for (int32_t i = 0; i < n; i++) n_tiles += (raw_off[i + 1] - raw_off[i] + abea::kEventTile - 1) / abea::kEventTile;
+    if (n_tiles > INT32_MAX) return ABEA_ERR_ARG;
+    const size_t meta_bytes = 3 * m * sizeof(int64_t) + (size_t)n * sizeof(abea_calib) + (size_t)n_tiles * 4;
     if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
     if ((rc = ensure_host(c->h_ev_meta, meta_bytes))) return rc;
-    int64_t *h_raw_off = (int64_t *)c->h_ev_meta.p, *h_ev_off = h_raw_off + m, *h_bits_off = h_ev_off + m,
-            *h_bnd_off = h_bits_off + m;
-    abea_calib *h_cal = (abea_calib *)(h_bnd_off + m);
-    h_bits_off[0] = 0;
-    h_bnd_off[0] = 0;
+    int64_t *h_raw_off = (int64_t *)c->h_ev_meta.p, *h_ev_off = h_raw_off + m, *h_tile_off = h_ev_off + m;
+    abea_calib *h_cal = (abea_calib *)(h_tile_off + m);
+    int32_t *h_tile_read = (int32_t *)(h_cal + n);
+    h_tile_off[0] = 0;
     for (int32_t i = 0; i < n; i++) {
-        const int64_t len = raw_off[i + 1] - raw_off[i];
+        const int64_t tiles = (raw_off[i + 1] - raw_off[i] + abea::kEventTile - 1) / abea::kEventTile;
         h_raw_off[i] = raw_off[i] - raw_off[0];
         h_ev_off[i] = event_off[i] - event_off[0];
-        h_bits_off[i + 1] = h_bits_off[i] + (len + 31) / 32;
-        h_bnd_off[i + 1] = h_bnd_off[i] + len / window + 3;
+        h_tile_off[i + 1] = h_tile_off[i] + tiles;
+        for (int64_t t = h_tile_off[i]; t < h_tile_off[i + 1]; t++) h_tile_read[t] = i;
         h_cal[i] = calib[i];
     }
     h_raw_off[n] = raw_off[n] - raw_off[0];
     h_ev_off[n] = event_off[n] - event_off[0];
     if ((rc = ensure_dev(c, c->ev_meta, meta_bytes, st))) return rc;
-    if ((rc = ensure_dev(c, c->ev_bits, std::max<size_t>((size_t)h_bits_off[n], 1) * 4, st))) return rc;
-    if ((rc = ensure_dev(c, c->ev_bnd, std::max<size_t>((size_t)h_bnd_off[n], 1) * abea::event_record_bytes(), st)))
-        return rc;
+    if ((rc = ensure_dev(c, c->ev_bits, std::max<int64_t>(n_tiles, 1) * abea::event_tile_bytes(), st))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->ev_meta.p, h_raw_off, meta_bytes, cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
     const int64_t *d_meta = (const int64_t *)c->ev_meta.p;
-    if ((rc = cuda_err((cudaError_t)abea::launch_events(
-             d_meta, n, d_raw + raw_off[0], (const abea_calib *)(d_meta + 4 * m), window, tau2,
-             (uint32_t *)c->ev_bits.p, d_meta + 2 * m, c->ev_bnd.p, d_meta + 3 * m, d_events + event_off[0], d_meta + m,
-             d_n_events, st))))
+    const abea_calib *d_cal = (const abea_calib *)(d_meta + 3 * m);
+    if ((rc = cuda_err((cudaError_t)abea::launch_events(d_meta, d_meta + m, d_meta + 2 * m,
+                                                         (const int32_t *)(d_cal + n), n, n_tiles,
+                                                         d_raw + raw_off[0], d_cal, window, tau2, c->ev_bits.p,
+                                                         d_events + event_off[0], d_n_events, st))))
         return rc;
-    c->last_launches++;
+    c->last_launches += n_tiles > 0 ? 3 : 1;
     return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+int abea_f32_from_i64(const int64_t *d_in, int64_t n, float *d_out, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_in || !d_out))) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    return cuda_err((cudaError_t)abea::launch_f32_from_i64(d_in, n, d_out, cuda_stream));
 }
 
 int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,

@@ -73,10 +73,16 @@ int launch_eventalign(const int64_t *meta, int32_t n, const uint8_t *seq, const 
                       const abea_scalings *sc, const abea_result *res, const int32_t *pairs, const int32_t *ref_pos,
                       const uint8_t *ref, int64_t ref_len, const ModelRow *model, int k, int scale_events,
                       abea_eventalign_row *rows, void *stream);
-int launch_events(const int64_t *raw_off, int32_t n, const int16_t *raw, const abea_calib *calib, int window,
-                  float tau2, uint32_t *bits, const int64_t *bits_off, void *bnd, const int64_t *bnd_off,
-                  abea_event *out, const int64_t *ev_off, int32_t *n_ev, void *stream);
-size_t event_record_bytes();
+// Event detection runs over tiles of kEventTile positions (a read of len
+// samples has ceil(len / kEventTile) tiles; tile_off is their prefix over the
+// reads, tile_read the read of each tile).  scratch holds event_tile_bytes()
+// per tile.  Three launches.
+constexpr int kEventTile = 4096;
+size_t event_tile_bytes();
+int launch_events(const int64_t *raw_off, const int64_t *ev_off, const int64_t *tile_off, const int32_t *tile_read,
+                  int32_t n, int64_t n_tiles, const int16_t *raw, const abea_calib *calib, int window, float tau2,
+                  void *scratch, abea_event *out, int32_t *n_ev, void *stream);
+int launch_f32_from_i64(const int64_t *in, int64_t n, float *out, void *stream);
 int launch_scalings(const int64_t *d_seq_off, const int64_t *d_ev_off, int32_t n, const uint8_t *seq,
                     const float *events, const ModelRow *model, int k, abea_scalings *out, int32_t *status,
                     void *stream);

@@ -10,12 +10,14 @@ from paper_2101_05012_gb300 import binding, synth
 pytestmark = pytest.mark.gpu
 
 
-def run(raws, calib, window, tau2, caps=None):
+def run(raws, calib, window, tau2, caps=None, lead=0):
+    """lead: samples (not part of any read) before the first read in the device array."""
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
-    raw = np.concatenate(raws).astype(np.int16) if raws else np.zeros(0, np.int16)
-    raw_off = np.zeros(len(raws) + 1, np.int64)
+    raw = np.concatenate([np.full(lead, 999, np.int16)] + list(raws)).astype(np.int16)
+    raw_off = np.full(len(raws) + 1, lead, np.int64)
     np.cumsum([len(r) for r in raws], out=raw_off[1:])
+    raw_off[1:] += lead
     if caps is None:
         caps = [len(r) // window + 2 for r in raws]
     ev_off = np.zeros(len(raws) + 1, np.int64)
@@ -31,8 +33,8 @@ def run(raws, calib, window, tau2, caps=None):
         return evs, ev_off, d_n.cpu().numpy()
 
 
-def compare(raws, calib, window, tau2, caps=None):
-    evs, ev_off, counts = run(raws, calib, window, tau2, caps)
+def compare(raws, calib, window, tau2, caps=None, lead=0):
+    evs, ev_off, counts = run(raws, calib, window, tau2, caps, lead)
     for i, x in enumerate(raws):
         m, s, a, L = eo.detect(x, window, tau2, calib[i])
         assert counts[i] == len(m), (i, counts[i], len(m))
@@ -78,3 +80,69 @@ def test_capacity_shorter_than_needed():
     caps = [f // 2 for f in full]
     evs, counts = compare(raws, rb.calib, 3, 2.0, caps)
     assert list(counts) == full
+
+
+TILE = 4096         # positions per tile of the device kernels
+
+
+def test_starts_at_tile_edges():
+    """Level changes on both sides of every tile edge (and exactly on it), reads one sample short of,
+    exactly at and one past whole tiles; the windows and the local-maximum rule straddle the edges."""
+    rng = np.random.default_rng(21)
+    raws = []
+    for n_tiles, delta in ((1, -1), (1, 0), (1, 1), (2, 0), (3, 5), (4, -3)):
+        n = n_tiles * TILE + delta
+        cuts = {0, n}
+        for e in range(1, n_tiles + 1):
+            for d in (-9, -4, 0, 3, 8):
+                if 0 < e * TILE + d < n:
+                    cuts.add(e * TILE + d)
+        cuts |= set(int(c) for c in rng.integers(1, n, 40))
+        cuts = sorted(cuts)
+        x = np.zeros(n, np.int16)
+        level = 500
+        for u, v in zip(cuts[:-1], cuts[1:]):
+            level += int(rng.choice([-1, 1])) * int(rng.integers(20, 200))
+            x[u:v] = level
+        x += rng.normal(0, 3, n).astype(np.int16)
+        raws.append(x)
+    calib = np.array([[0.5, 0.25]] * len(raws), np.float32)
+    for w in (2, 3, 8):
+        for tau2 in (0.0, 3.0):
+            evs, counts = compare(raws, calib, w, tau2)
+            assert counts.min() > 10
+
+
+def test_offset_batch_and_long_read():
+    """The batch starts at sample 7 of the device array; one read spans 30 tiles."""
+    rb = synth.make_raw_batch("batch_4096_ln5kb", read_ids=range(0, 4096, 512))
+    raws = [rb.signal(i) for i in range(rb.n)]
+    rng = np.random.default_rng(4)
+    long = np.repeat(rng.integers(100, 900, 9000), rng.integers(5, 22, 9000)).astype(np.int16)[:30 * TILE - 11]
+    raws.append(long + rng.normal(0, 6, len(long)).astype(np.int16))
+    calib = np.concatenate([rb.calib, [[1.0, 0.5]]]).astype(np.float32)
+    compare(raws, calib, 3, 2.0, lead=7)
+
+
+def test_integer_to_float_rounding():
+    """The event kernels' own int64 -> float rounding against IEEE round-to-nearest-even (numpy's
+    conversion on the host) and the platform's conversion on the device: every magnitude, the exact
+    halfway cases with even and odd kept significands, and one above and below each."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(13)
+    v = [np.arange(-70000, 70000, dtype=np.int64)]
+    for e in range(24, 63):
+        base = rng.integers(1 << 23, 1 << 24, 2000, dtype=np.int64) << (e - 23)
+        half = np.int64(1) << (e - 24)
+        v += [base, base + half, base - half, base + half + 1, base + half - 1, base + 1, base - 1,
+              rng.integers(1 << e, (1 << e) * 2 - 1, 4000, dtype=np.int64)]
+    v = np.concatenate(v)
+    v = np.concatenate([v, -v[v > 0]])
+    d_in = torch.from_numpy(v).to(dev)
+    d_out = torch.empty(len(v), dtype=torch.float32, device=dev)
+    binding.f32_from_i64(d_in, d_out)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), v.astype(np.float32).view(np.uint32))
+    assert np.array_equal(got.view(np.uint32), d_in.to(torch.float32).cpu().numpy().view(np.uint32))
