@@ -509,8 +509,8 @@ def run_ours(args):
     ea_ms = a0.elapsed_time(a1) / args.steps
     rows_n = int(res["n_pairs"].sum())
     ea_bytes = rows_n * (8 + 4 + 4 + 40)
-    eventalign_line = {"kernel": "eventalign_kernel", "rows": rows_n, "ms_per_launch": ea_ms,
-                       "rows_per_s": rows_n / (ea_ms / 1e3),
+    eventalign_line = {"kernels": ["eventalign_ranks_kernel", "eventalign_kernel"], "rows": rows_n,
+                       "ms_per_call": ea_ms, "launches_per_call": 2, "rows_per_s": rows_n / (ea_ms / 1e3),
                        "roofline": {"bound": "hbm", "achieved": ea_bytes / (ea_ms / 1e3) / 1e9, "peak": hbm,
                                     "unit": "GB/s", "frac": ea_bytes / (ea_ms / 1e3) / 1e9 / hbm,
                                     "bytes_per_launch": ea_bytes}}

@@ -51,8 +51,8 @@ struct abea_ctx {
     size_t budget = 0;
     size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
     int k = 0;
-    DevBuf model;
-    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ea_meta;
+    DevBuf model, model_f;             // model rows; level mean and stdv as float2
+    DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ea_meta, ea_ranks;
     DevBuf events, seq, res, pairs;   // staging of the host-memory calls
     HostBuf h_rd, h_order, h_events, h_seq, h_res, h_pairs, h_offs, h_ev_meta, h_ea_meta;
     cudaEvent_t t0 = nullptr, t1 = nullptr, upload_done = nullptr, batch_done = nullptr;
@@ -420,9 +420,9 @@ void abea_destroy(abea_ctx *c)
     cudaSetDevice(c->device);
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     cudaDeviceSynchronize();
-    DevBuf *dev[] = {&c->model, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
+    DevBuf *dev[] = {&c->model, &c->model_f, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
                      &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs, &c->ev_meta, &c->ev_bits,
-                     &c->ea_meta};
+                     &c->ea_meta, &c->ea_ranks};
     for (DevBuf *b : dev) free_dev(*b);
     HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs,
                        &c->h_ev_meta, &c->h_ea_meta};
@@ -465,6 +465,18 @@ int abea_set_model(abea_ctx *c, int k, const float *level_mean, const float *lev
     }
     int rc = cuda_err(cudaMemcpy(c->model.p, m.data(), rows * sizeof(ModelRow), cudaMemcpyHostToDevice));
     if (rc) return rc;
+    std::vector<float2> mf(rows);
+    for (size_t r = 0; r < rows; r++) mf[r] = make_float2(level_mean[r], level_stdv[r]);
+    if (c->model_f.cap < rows * sizeof(float2)) {
+        free_dev(c->model_f);
+        if (cudaMalloc(&c->model_f.p, rows * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            return ABEA_ERR_NOMEM;
+        }
+        c->model_f.cap = rows * sizeof(float2);
+    }
+    if ((rc = cuda_err(cudaMemcpy(c->model_f.p, mf.data(), rows * sizeof(float2), cudaMemcpyHostToDevice))))
+        return rc;
     c->k = k;
     c->h_mean.assign(level_mean, level_mean + rows);
     c->h_stdv.assign(level_stdv, level_stdv + rows);
@@ -685,14 +697,16 @@ int abea_eventalign(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t 
     std::memcpy(h + 2 * m, pair_off, m * sizeof(int64_t));
     std::memcpy(h + 3 * m, sc, (size_t)n * sizeof(abea_scalings));
     if ((rc = ensure_dev(c, c->ea_meta, bytes, st))) return rc;
+    if ((rc = ensure_dev(c, c->ea_ranks, std::max<int64_t>(seq_off[n] - seq_off[0], 1) * sizeof(int2), st))) return rc;
     if ((rc = cuda_err(cudaMemcpyAsync(c->ea_meta.p, h, bytes, cudaMemcpyHostToDevice, st)))) return rc;
     if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
     const int64_t *d_meta = (const int64_t *)c->ea_meta.p;
     if ((rc = cuda_err((cudaError_t)abea::launch_eventalign(
-             d_meta, n, d_seq, d_events, (const abea_scalings *)(d_meta + 3 * m), d_results, d_pairs, d_ref_pos, d_ref,
-             ref_len, (const ModelRow *)c->model.p, c->k, scale_events ? 1 : 0, d_rows, st))))
+             d_meta, n, pair_off[n] - pair_off[0], d_seq, seq_off[0], seq_off[n], (int2 *)c->ea_ranks.p, d_events,
+             (const abea_scalings *)(d_meta + 3 * m), d_results, d_pairs, d_ref_pos, d_ref, ref_len,
+             (const float2 *)c->model_f.p, c->k, scale_events ? 1 : 0, d_rows, st))))
         return rc;
-    c->last_launches++;
+    c->last_launches += 2;
     return cuda_err(cudaEventRecord(c->batch_done, st));
 }
 
@@ -786,7 +800,7 @@ int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const i
     if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
     const int64_t *d_off = (const int64_t *)c->offs.p;
     if ((rc = cuda_err((cudaError_t)abea::launch_scalings(d_off, d_off + n + 1, n, d_seq, d_events,
-                                                           (const ModelRow *)c->model.p, c->k, d_out, d_status,
+                                                           (const float2 *)c->model_f.p, c->k, d_out, d_status,
                                                            st))))
         return rc;
     c->last_launches++;

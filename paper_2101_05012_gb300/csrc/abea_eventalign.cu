@@ -15,9 +15,12 @@
 // ref_rank the rank of ref[ref_pos : ref_pos+k] (-1 if unaligned, past the
 // reference end or not ACGT).
 //
-// One block per read; the threads take its pairs in turn.  Gather-bound: per
-// pair 8 B of pair, 4 B of event, a model row (L2), the read's and the
-// reference's k bases (L1) and 40 B of record.
+// Two launches: the k-mer ranks of every read position (read and reference),
+// then the rows.  Per row: 8 B of pair, 4 B of event, 4 B of reference
+// position, 8 B of ranks, a model entry (shared memory for k <= 6) and 40 B
+// of record.
+#include <algorithm>
+
 #include "abea_internal.h"
 
 namespace abea {
@@ -26,80 +29,237 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ int rank_of(const uint8_t *s, int k)
+// c is one of A C G T: c - 'A' is 0, 2, 6 or 19.
+__device__ __forceinline__ bool is_base(unsigned c)
 {
-    int r = 0;
-    for (int j = 0; j < k; j++) {
-        const unsigned c = s[j];
-        const unsigned d = c - 'A';
-        if (!(d < 32u && ((0x80045u >> d) & 1u))) return -1;   // A C G T only
-        r = 4 * r + (int)(((c >> 1) ^ (c >> 2)) & 3u);
-    }
-    return r;
+    const unsigned d = c - 'A';
+    return d < 32u && ((0x80045u >> d) & 1u);
 }
 
-__global__ void __launch_bounds__(kThreads) eventalign_kernel(const int64_t *meta, int32_t n, const uint8_t *seq,
-                                                            const float *events, const abea_scalings *sc,
-                                                            const abea_result *res, const int32_t *pairs,
-                                                            const int32_t *ref_pos, const uint8_t *ref,
-                                                            int64_t ref_len, const ModelRow *model, int k,
+// 2-bit code of an ACGT base: ((c >> 1) ^ (c >> 2)) & 3 maps A C G T to 0 1 2 3.
+__device__ __forceinline__ unsigned base_code(unsigned c) { return ((c >> 1) ^ (c >> 2)) & 3u; }
+
+constexpr int kPasses = 8;                         // passes of 256 per chunk
+constexpr int kChunk = kThreads * kPasses;         // positions or pair slots per chunk
+
+// The last i with off[i] <= x (off ascending, off[0] <= x < off[n]).
+__device__ __forceinline__ int find_read(const int64_t *off, int n, int64_t x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Rank of the k bases at s (A C G T = 0 1 2 3, the first base most
+// significant); -1 if one of them is not A, C, G or T.  code[c]: the 2-bit
+// code of byte c, or 4 if c is not a base.
+__device__ __forceinline__ int rank_of(const uint8_t *s, int k, const uint8_t *code)
+{
+    unsigned r = 0, bad = 0;
+    for (int j = 0; j < k; j++) {
+        const unsigned c = code[s[j]];
+        bad |= c;
+        r = (r << 2) | (c & 3u);
+    }
+    return (bad & 4u) ? -1 : (int)r;
+}
+
+// Launch 1: for every k-mer start q of an aligned read, the rank of the read's
+// k-mer and of the reference k-mer at ref_pos[q] (-1 if unaligned, past the
+// reference end or not ACGT), into ranks[seq_off[i] - seq_lo + q].  The grid
+// runs over chunks of 2,048 bases of the batch, each warp 256 of them, one
+// position per lane and pass, so that a warp's loads cover consecutive bases.
+__global__ void __launch_bounds__(kThreads) eventalign_ranks_kernel(const int64_t *meta, int32_t n, int64_t n_chunks,
+                                                                  const uint8_t *seq, int64_t seq_lo,
+                                                                  const abea_result *res, const int32_t *ref_pos,
+                                                                  const uint8_t *ref, int64_t ref_len, int k,
+                                                                  int2 *ranks)
+{
+    __shared__ uint8_t code[256];
+    for (int c = threadIdx.x; c < 256; c += kThreads) code[c] = is_base((unsigned)c) ? (uint8_t)base_code(c) : 4;
+    __syncthreads();
+    const int64_t *seq_off = meta;
+    const int64_t end = seq_off[n];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        // warp w takes positions c0 + 256 w .. c0 + 256 w + 255, 32 per pass
+        const int64_t w0 = seq_lo + c * kChunk + (int64_t)kThreads * warp;
+        if (w0 >= end) continue;
+        int rd = __shfl_sync(0xffffffffu, lane == 0 ? find_read(seq_off, n, w0) : 0, 0), cur = -1;
+        bool ok = false;
+        int64_t last = 0;                          // the read's last k-mer start + 1
+        for (int j = 0; j < kPasses; j++) {
+            const int64_t g = w0 + 32 * j + lane;
+            if (g >= end) break;
+            while (g >= seq_off[rd + 1]) rd++;
+            if (rd != cur) {
+                cur = rd;
+                ok = res[rd].status == ABEA_READ_OK;
+                last = seq_off[rd + 1] - k + 1;
+            }
+            if (!ok || g >= last) continue;
+            const int pos = ref_pos[g];
+            const int rr = (pos >= 0 && (int64_t)pos + k <= ref_len) ? rank_of(ref + pos, k, code) : -1;
+            ranks[g - seq_lo] = make_int2(rank_of(seq + g, k, code), rr);
+        }
+    }
+}
+
+constexpr int kRowWords = (int)(sizeof(abea_eventalign_row) / 4);
+constexpr int kSmemModelRanks = 4096;              // models up to k = 6 sit in shared memory
+static_assert(sizeof(abea_eventalign_row) == 40, "row layout");
+
+// Launch 2.  The grid runs over chunks of 2,048 pair slots of the whole
+// batch (the slots of read i are pair_off[i] .. pair_off[i+1]); a block takes
+// chunks in turn, each warp 256 consecutive slots of a chunk, 32 per pass.
+// Each warp forms its 32 slots' rows in its own shared-memory stage and writes the valid ones as consecutive words, so that
+// a store covers whole lines.  SMEM_MODEL: the model's (mean, stdv) table is
+// copied into shared memory once per block.
+template <bool SMEM_MODEL, bool WORD8>
+__global__ void __launch_bounds__(kThreads, 5) eventalign_kernel(const int64_t *meta, int32_t n, int64_t n_chunks,
+                                                            int64_t seq_lo, const float *events,
+                                                            const abea_scalings *sc, const abea_result *res,
+                                                            const int32_t *pairs, const int32_t *ref_pos,
+                                                            const int2 *ranks, const float2 *model_f, int k,
                                                             int scale_events, abea_eventalign_row *rows)
 {
-    const int i = blockIdx.x;
-    if (i >= n) return;
+    __shared__ float2 smodel[SMEM_MODEL ? kSmemModelRanks : 1];
+    __shared__ __align__(16) abea_eventalign_row stage[kThreads];
     const int64_t *seq_off = meta, *ev_off = meta + (n + 1), *pair_off = meta + 2 * (n + 1);
-    const abea_result r = res[i];
-    if (r.status != ABEA_READ_OK) return;
-    const int np = r.n_pairs;
-    const uint8_t *sq = seq + seq_off[i];
-    const int32_t *rp = ref_pos + seq_off[i];
-    const float *ev = events + ev_off[i];
-    const int2 *pr = reinterpret_cast<const int2 *>(pairs) + pair_off[i];
-    abea_eventalign_row *out = rows + pair_off[i];
-    const abea_scalings s = sc[i];
-    for (int t = threadIdx.x; t < np; t += kThreads) {
-        const int2 p = pr[t];
-        const float x = ev[p.x];
-        const int mr = rank_of(sq + p.y, k);     // a valid k-mer: the read aligned
-        const ModelRow row = model[mr < 0 ? 0 : mr];
-        const float mu = (float)row.mu, sd = (float)row.sd;   // exact: the model is FP32
-        float level, mean, stdv;
-        if (scale_events) {
-            level = __fdiv_rn(__fsub_rn(x, s.shift), s.scale);
-            mean = mu;
-            stdv = __fdiv_rn(__fmul_rn(sd, s.var), s.scale);
-        } else {
-            level = x;
-            mean = __fadd_rn(__fmul_rn(mu, s.scale), s.shift);
-            stdv = __fmul_rn(sd, s.var);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (SMEM_MODEL) {
+        for (int r = t; r < (1 << (2 * k)); r += kThreads) smodel[r] = model_f[r];
+        __syncthreads();
+    }
+    const float2 *mdl = SMEM_MODEL ? smodel : model_f;
+    abea_eventalign_row *my_stage = stage + 32 * warp;
+    const int64_t end = pair_off[n];
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        // warp w takes slots c0 + 256 w .. c0 + 256 w + 255, 32 per pass
+        const int64_t w0 = pair_off[0] + c * kChunk + (int64_t)kThreads * warp;
+        if (w0 >= end) continue;
+        int rd = __shfl_sync(0xffffffffu, lane == 0 ? find_read(pair_off, n, w0) : 0, 0), cur = -1;
+        int np = 0;
+        bool ok = false;
+        int64_t p0 = 0;
+        const int2 *rk = nullptr;
+        const int32_t *rp = nullptr;
+        const float *ev = nullptr;
+        abea_scalings s{};
+        for (int j = 0; j < kPasses; j++) {
+            const int64_t wfirst = w0 + 32 * j;                              // the pass's first slot
+            if (wfirst >= end) break;                                        // whole warps
+            const int64_t slot = wfirst + lane;
+            bool valid = false;
+            if (slot < end) {
+                while (slot >= pair_off[rd + 1]) rd++;
+                if (rd != cur) {
+                    cur = rd;
+                    const abea_result r = res[rd];
+                    ok = r.status == ABEA_READ_OK;
+                    np = r.n_pairs;
+                    p0 = pair_off[rd];
+                    rk = ranks + (seq_off[rd] - seq_lo);
+                    rp = ref_pos + seq_off[rd];
+                    ev = events + ev_off[rd];
+                    s = sc[rd];
+                }
+                const int64_t q = slot - p0;
+                if (ok && q < np) {
+                    valid = true;
+                    const int2 p = reinterpret_cast<const int2 *>(pairs)[slot];
+                    const float x = ev[p.x];
+                    const int pos = rp[p.y];
+                    const int2 rank = rk[p.y];
+                    const int mr = rank.x, rr = rank.y;   // mr >= 0: the read aligned, so its bases are ACGT
+                    const float2 row = mdl[mr < 0 ? 0 : mr];
+                    const float mu = row.x, sd = row.y;
+                    float level, mean, stdv;
+                    if (scale_events) {
+                        level = __fdiv_rn(__fsub_rn(x, s.shift), s.scale);
+                        mean = mu;
+                        stdv = __fdiv_rn(__fmul_rn(sd, s.var), s.scale);
+                    } else {
+                        level = x;
+                        mean = __fadd_rn(__fmul_rn(mu, s.scale), s.shift);
+                        stdv = __fmul_rn(sd, s.var);
+                    }
+                    abea_eventalign_row o;
+                    o.read = rd;
+                    o.event = p.x;
+                    o.kmer = p.y;
+                    o.ref_pos = pos;
+                    o.ref_rank = rr;
+                    o.model_rank = mr;
+                    o.level = level;
+                    o.model_mean = mean;
+                    o.model_stdv = stdv;
+                    o.z = __fdiv_rn(__fsub_rn(level, mean), stdv);
+                    my_stage[lane] = o;
+                }
+            }
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            __syncwarp();
+            // the warp's rows out as consecutive words (8 or 4 bytes), valid rows only
+            if (WORD8) {
+                const uint2 *src = reinterpret_cast<const uint2 *>(my_stage);
+                uint2 *dst = reinterpret_cast<uint2 *>(rows + wfirst);
+#pragma unroll
+                for (int m = 0; m < kRowWords / 2; m++) {
+                    const int w = lane + 32 * m, row = w / (kRowWords / 2);
+                    if ((vb >> row) & 1u) dst[w] = src[w];
+                }
+            } else {
+                const unsigned *src = reinterpret_cast<const unsigned *>(my_stage);
+                unsigned *dst = reinterpret_cast<unsigned *>(rows + wfirst);
+#pragma unroll
+                for (int m = 0; m < kRowWords; m++) {
+                    const int w = lane + 32 * m, row = w / kRowWords;
+                    if ((vb >> row) & 1u) dst[w] = src[w];
+                }
+            }
+            __syncwarp();
         }
-        const int pos = rp[p.y];
-        const int rr = (pos >= 0 && (int64_t)pos + k <= ref_len) ? rank_of(ref + pos, k) : -1;
-        abea_eventalign_row o;
-        o.read = i;
-        o.event = p.x;
-        o.kmer = p.y;
-        o.ref_pos = pos;
-        o.ref_rank = rr;
-        o.model_rank = mr;
-        o.level = level;
-        o.model_mean = mean;
-        o.model_stdv = stdv;
-        o.z = __fdiv_rn(__fsub_rn(level, mean), stdv);
-        out[t] = o;
     }
 }
 
 }  // namespace
 
-int launch_eventalign(const int64_t *meta, int32_t n, const uint8_t *seq, const float *events,
-                      const abea_scalings *sc, const abea_result *res, const int32_t *pairs, const int32_t *ref_pos,
-                      const uint8_t *ref, int64_t ref_len, const ModelRow *model, int k, int scale_events,
-                      abea_eventalign_row *rows, void *stream)
+int launch_eventalign(const int64_t *meta, int32_t n, int64_t total_slots, const uint8_t *seq, int64_t seq_lo,
+                      int64_t seq_hi, int2 *ranks, const float *events, const abea_scalings *sc, const abea_result *res, const int32_t *pairs,
+                      const int32_t *ref_pos, const uint8_t *ref, int64_t ref_len, const float2 *model_f, int k,
+                      int scale_events, abea_eventalign_row *rows, void *stream)
 {
-    if (n <= 0) return (int)cudaSuccess;
-    eventalign_kernel<<<n, kThreads, 0, (cudaStream_t)stream>>>(meta, n, seq, events, sc, res, pairs, ref_pos, ref,
-                                                               ref_len, model, k, scale_events, rows);
+    if (n <= 0 || total_slots <= 0) return (int)cudaSuccess;
+    if (k < 1 || k > 12) return (int)cudaErrorInvalidValue;
+    const int64_t n_chunks = (total_slots + kChunk - 1) / kChunk;
+    const bool smem_model = (1 << (2 * k)) <= kSmemModelRanks;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    // resident blocks per SM: 5 with the 43 KB of shared memory of the model copy, else 8
+    const unsigned grid = (unsigned)std::min<int64_t>(n_chunks, (int64_t)sms * (smem_model ? 5 : 8));
+    const bool word8 = ((uintptr_t)rows & 7) == 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n_bases = seq_hi - seq_lo, rank_chunks = (n_bases + kChunk - 1) / kChunk;
+    if (rank_chunks > 0)
+        eventalign_ranks_kernel<<<(unsigned)std::min<int64_t>(rank_chunks, (int64_t)sms * 8), kThreads, 0, st>>>(
+            meta, n, rank_chunks, seq, seq_lo, res, ref_pos, ref, ref_len, k, ranks);
+#define ABEA_EA_LAUNCH(sm_, w8_) \
+    eventalign_kernel<sm_, w8_><<<grid, kThreads, 0, st>>>(meta, n, n_chunks, seq_lo, events, sc, res, pairs, ref_pos, \
+                                                           ranks, model_f, k, scale_events, rows)
+    if (smem_model) {
+        if (word8) ABEA_EA_LAUNCH(true, true);
+        else ABEA_EA_LAUNCH(true, false);
+    } else {
+        if (word8) ABEA_EA_LAUNCH(false, true);
+        else ABEA_EA_LAUNCH(false, false);
+    }
+#undef ABEA_EA_LAUNCH
     return (int)cudaGetLastError();
 }
 

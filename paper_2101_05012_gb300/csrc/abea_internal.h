@@ -69,10 +69,13 @@ struct AlignArgs {
 int launch_prep(const ReadDesc *rd, int32_t n, const uint8_t *seq, const float *events,
                 const ModelRow *model, int k, float4 *kc, int32_t *flags, void *stream);
 int launch_align(const AlignArgs &a, const Geometry &g, int grid, void *stream);
-int launch_eventalign(const int64_t *meta, int32_t n, const uint8_t *seq, const float *events,
-                      const abea_scalings *sc, const abea_result *res, const int32_t *pairs, const int32_t *ref_pos,
-                      const uint8_t *ref, int64_t ref_len, const ModelRow *model, int k, int scale_events,
-                      abea_eventalign_row *rows, void *stream);
+// model_f: the model's level mean and stdv as floats, one float2 per k-mer rank.
+// The batch's bases are seq[seq_lo .. seq_hi); ranks: scratch of one int2 per
+// base; total_slots = pair_off[n] - pair_off[0].
+int launch_eventalign(const int64_t *meta, int32_t n, int64_t total_slots, const uint8_t *seq, int64_t seq_lo,
+                      int64_t seq_hi, int2 *ranks, const float *events, const abea_scalings *sc, const abea_result *res, const int32_t *pairs,
+                      const int32_t *ref_pos, const uint8_t *ref, int64_t ref_len, const float2 *model_f, int k,
+                      int scale_events, abea_eventalign_row *rows, void *stream);
 // Event detection runs over tiles of kEventTile positions (a read of len
 // samples has ceil(len / kEventTile) tiles; tile_off is their prefix over the
 // reads, tile_read the read of each tile).  scratch holds event_tile_bytes()
@@ -84,7 +87,7 @@ int launch_events(const int64_t *raw_off, const int64_t *ev_off, const int64_t *
                   void *scratch, abea_event *out, int32_t *n_ev, void *stream);
 int launch_f32_from_i64(const int64_t *in, int64_t n, float *out, void *stream);
 int launch_scalings(const int64_t *d_seq_off, const int64_t *d_ev_off, int32_t n, const uint8_t *seq,
-                    const float *events, const ModelRow *model, int k, abea_scalings *out, int32_t *status,
+                    const float *events, const float2 *model_f, int k, abea_scalings *out, int32_t *status,
                     void *stream);
 int align_grid_size(const Geometry &g, int device);
 

@@ -16,8 +16,9 @@
 // running sum is a pair (hi, lo) of floats, each addition an error-free
 // TwoSum (Knuth: hi + x = s + err exactly) whose error goes into lo, and each
 // square an error-free product (p = x*x, fma(x, x, -p) = its rounding error).
-// The pairs (about 48 significant bits) are combined in FP64 across the
-// block; the variance is E[x^2] - E[x]^2 in FP64 (the cancellation costs a
+// The pairs (about 48 significant bits) merge the same way across the block
+// and only the block's sums are widened to FP64; the variance is
+// E[x^2] - E[x]^2 in FP64 (the cancellation costs a
 // few bits of 53).  The results agree with the two-pass FP64 definition to
 // within a float rounding.
 #include "abea_internal.h"
@@ -27,20 +28,6 @@ namespace abea {
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ double block_sum(double v, double *red)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();                        // red is free again
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; w++) s += red[w];
-    return s;
-}
 
 // 2-bit code of an ACGT base, branch-free: ((c >> 1) ^ (c >> 2)) & 3 maps the
 // ASCII codes of A C G T to 0 1 2 3.
@@ -71,15 +58,48 @@ struct DSum {
         add(p);
         lo = __fadd_rn(lo, pe);
     }
+    // this + o, error-free on the hi parts
+    __device__ __forceinline__ void merge(const DSum &o)
+    {
+        add(o.hi);
+        lo = __fadd_rn(lo, o.lo);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// The sum over the block of every thread's pair, as a double in every thread:
+// the pairs merge in FP32 (a warp tree, then the warps' results in order), and
+// only the block's result is widened.
+__device__ __forceinline__ double block_sum(DSum v, float2 *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DSum w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v.merge(w);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();                        // red is free again
+    if (lane == 0) red[warp] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    DSum s;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) {
+        DSum t;
+        t.hi = red[w].x;
+        t.lo = red[w].y;
+        s.merge(t);
+    }
+    return s.value();
+}
+
 __global__ void __launch_bounds__(kThreads) scalings_kernel(const int64_t *seq_off, const int64_t *ev_off, int32_t n,
                                                           const uint8_t *seq, const float *events,
-                                                          const ModelRow *model, int k, abea_scalings *out,
+                                                          const float2 *model_f, int k, abea_scalings *out,
                                                           int32_t *status)
 {
-    __shared__ double red[kThreads / 32];
+    __shared__ float2 red[kThreads / 32];
     const int i = blockIdx.x;
     if (i >= n) return;
     const int64_t n_e = ev_off[i + 1] - ev_off[i];
@@ -111,16 +131,17 @@ __global__ void __launch_bounds__(kThreads) scalings_kernel(const int64_t *seq_o
             const unsigned c = sq[t + k - 1];
             if (!is_base(c)) bad = 1;
             r = ((r << 2) | base_code(c)) & mask;
-            const float mu = (float)model[r].mu;  // exact: the model means are floats
+            const float mu = model_f[r].x;
             sm.add(mu);
             qm.add_square(mu);
         }
     }
     bad = __syncthreads_or(bad);
-    const double s_e = block_sum(bad ? 0.0 : se.value(), red);
-    const double q_e = block_sum(bad ? 0.0 : qe.value(), red);
-    const double s_m = block_sum(bad ? 0.0 : sm.value(), red);
-    const double q_m = block_sum(bad ? 0.0 : qm.value(), red);
+    if (bad) se = qe = sm = qm = DSum();
+    const double s_e = block_sum(se, red);
+    const double q_e = block_sum(qe, red);
+    const double s_m = block_sum(sm, red);
+    const double q_m = block_sum(qm, red);
     if (threadIdx.x == 0) {
         abea_scalings s;
         s.var = 1.0f;
@@ -151,11 +172,11 @@ __global__ void __launch_bounds__(kThreads) scalings_kernel(const int64_t *seq_o
 }  // namespace
 
 int launch_scalings(const int64_t *d_seq_off, const int64_t *d_ev_off, int32_t n, const uint8_t *seq,
-                    const float *events, const ModelRow *model, int k, abea_scalings *out, int32_t *status,
+                    const float *events, const float2 *model_f, int k, abea_scalings *out, int32_t *status,
                     void *stream)
 {
     if (n <= 0) return (int)cudaSuccess;
-    scalings_kernel<<<n, kThreads, 0, (cudaStream_t)stream>>>(d_seq_off, d_ev_off, n, seq, events, model, k, out,
+    scalings_kernel<<<n, kThreads, 0, (cudaStream_t)stream>>>(d_seq_off, d_ev_off, n, seq, events, model_f, k, out,
                                                               status);
     return (int)cudaGetLastError();
 }

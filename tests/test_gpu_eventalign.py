@@ -28,6 +28,7 @@ def test_rows_match_the_oracle():
         refs.append(r)
         base += len(r)
     ref = np.concatenate(refs)
+    ref[::97] = ord("N")                    # reference k-mers over a non-ACGT base get no rank
     po = binding.pair_offsets(b.n_events(), np.maximum(b.n_kmers(), 1))
     with binding.Context(0) as ctx:
         ctx.set_model(b.k, b.model_mean, b.model_stdv)
@@ -66,3 +67,4 @@ def test_rows_match_the_oracle():
                 assert np.array_equal(g[f], want[f]), (mode, i, f)
     # the reference positions of the k-mers are shifted by the read's indels, and some bases are insertions
     assert np.any(out[False]["ref_pos"] < 0)
+    assert np.any((out[False]["ref_pos"] >= 0) & (out[False]["ref_rank"] < 0))
