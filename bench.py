@@ -384,7 +384,7 @@ def run_ours(args):
 
     # end to end through the host-memory call (abea_align_packed, page-locked host buffers): one host
     # thread per context, each call copies its inputs in and its results out
-    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 60))
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     h_seq, h_ev = pin(batch.seq), pin(batch.events)
     h_out = [torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy() for _ in range(D)]
