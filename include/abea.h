@@ -218,7 +218,9 @@ int abea_f32_from_i64(const int64_t *d_in, int64_t n, float *d_out, void *cuda_s
  * those of the model level means (ctx's model) along its k-mers:
  *   d_out[i] = { scale = sqrt(v_e / v_m), shift = m_e - scale * m_m, var = 1 },
  * d_status[i] = ABEA_SCALE_OK; degenerate and rejected reads as the
- * ABEA_SCALE_* codes say.  Computed in FP64, rounded once to float.  Bulk data
+ * ABEA_SCALE_* codes say.  The sums carry about 48 significant bits (error-
+ * free FP32 pairs), the moments and the square root are FP64, and each
+ * result is within one float ulp of the FP64 definition rounded once.  Bulk data
  * as in abea_align_batch_device: d_seq, d_events, d_out (abea_scalings[n])
  * and d_status (int32[n]) are device pointers, seq_off and ev_off host
  * arrays; enqueued on cuda_stream without waiting. */
