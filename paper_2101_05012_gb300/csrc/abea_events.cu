@@ -420,7 +420,7 @@ constexpr int kEmitSmem = (kXsWords * 4 > kMaxRec * (int)sizeof(Rec)) ? kXsWords
 // events t, t + 256, ... of the tile: event e runs from record e-1 (the last
 // start before the tile for e = 0) to record e (the end of the read after the
 // read's last record).
-__global__ void __launch_bounds__(kThreads, 5) event_emit_kernel(const int64_t *raw_off, const int64_t *tile_off,
+__global__ void __launch_bounds__(kThreads, 6) event_emit_kernel(const int64_t *raw_off, const int64_t *tile_off,
                                                             const int32_t *tile_read, const int64_t *ev_off,
                                                             const int16_t *raw, const abea_calib *calib,
                                                             const uint32_t *bits, const Run *tpre, abea_event *out)
