@@ -196,7 +196,7 @@ __device__ __forceinline__ float t2_value(int p, int n, int SL, int SR, long lon
 // a + 16t + 15, rolling the four window sums from registers, then decides the
 // same positions from the t2 values around them.
 template <int W>
-__global__ void __launch_bounds__(kThreads, 5) event_tiles_kernel(const int64_t *raw_off, const int64_t *tile_off,
+__global__ void __launch_bounds__(kThreads, 6) event_tiles_kernel(const int64_t *raw_off, const int64_t *tile_off,
                                                              const int32_t *tile_read, const int16_t *raw,
                                                              float tau2, uint32_t *bits, Run *tsum)
 {
