@@ -68,3 +68,50 @@ def test_rows_match_the_oracle():
     # the reference positions of the k-mers are shifted by the read's indels, and some bases are insertions
     assert np.any(out[False]["ref_pos"] < 0)
     assert np.any((out[False]["ref_pos"] >= 0) & (out[False]["ref_rank"] < 0))
+
+
+@pytest.mark.parametrize("workload,rows_offset", [("wide_10k_ln10kb_k9_w200", 0), ("plain_64x1kb", 4)])
+def test_global_model_and_unaligned_rows(workload, rows_offset):
+    """k = 9 (the model table stays in global memory) and a row buffer that starts 4 bytes past an
+    8-byte boundary (rows written as 4-byte words): every field identical to the oracle."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    b = synth.make_batch(workload, n_reads=16)
+    refs, pos = [], np.zeros(len(b.seq), np.int32)
+    base = 0
+    for i in range(b.n):
+        r, p = synth.make_ref_alignment(b.seq[b.seq_off[i]:b.seq_off[i + 1]].tobytes(), 5, i)
+        pos[b.seq_off[i]:b.seq_off[i + 1]] = np.where(p >= 0, p + base, -1)
+        refs.append(r)
+        base += len(r)
+    ref = np.concatenate(refs)
+    po = binding.pair_offsets(b.n_events(), np.maximum(b.n_kmers(), 1))
+    with binding.Context(0) as ctx:
+        ctx.set_model(b.k, b.model_mean, b.model_stdv)
+        d_seq = torch.from_numpy(b.seq).to(dev)
+        d_ev = torch.from_numpy(b.events).to(dev)
+        d_res = torch.zeros(b.n * 24, dtype=torch.uint8, device=dev)
+        d_pairs = torch.zeros(int(po[-1]) * 2, dtype=torch.int32, device=dev)
+        d_pos = torch.from_numpy(pos).to(dev)
+        d_ref = torch.from_numpy(ref).to(dev)
+        s = torch.cuda.Stream(dev)
+        ctx.align_batch_device(b.n, b.W, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_res, d_pairs, po,
+                               stream=s.cuda_stream)
+        store = torch.zeros(int(po[-1]) * 40 + 8, dtype=torch.uint8, device=dev)
+        d_rows = store[rows_offset:rows_offset + int(po[-1]) * 40]
+        assert d_rows.data_ptr() % 8 == rows_offset
+        ctx.eventalign(b.n, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_res, d_pairs, po, d_pos, d_ref,
+                       len(ref), True, d_rows, stream=s.cuda_stream)
+        s.synchronize()
+        rows = np.frombuffer(d_rows.cpu().numpy().tobytes(), binding.EVENTALIGN_DTYPE)
+        res = binding.results_from_bytes(d_res.cpu().numpy())
+        pairs = d_pairs.cpu().numpy().reshape(-1, 2)
+    assert np.all(res["status"] == 0)
+    for i in range(b.n):
+        n = int(res["n_pairs"][i])
+        e, sq, sc = b.read(i)
+        want = ea.rows(i, b.model_mean, b.model_stdv, b.k, sq, e, sc, pairs[po[i]:po[i] + n], ref,
+                       pos[b.seq_off[i]:b.seq_off[i + 1]], scale_events=True)
+        got = rows[po[i]:po[i] + n]
+        for f in binding.EVENTALIGN_DTYPE.names:
+            assert np.array_equal(got[f], want[f]), (workload, i, f)
