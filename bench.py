@@ -294,10 +294,10 @@ def run_ours(args):
     from paper_2101_05012_gb300 import binding, synth
 
     rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)            # before the process group: NCCL binds the current device
+    dev = torch.device("cuda", local_rank)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
     if args.max_bases:
         L = synth.read_lengths(synth.WORKLOADS[args.workload])
         batch = synth.make_batch(args.workload, read_ids=np.nonzero(L <= args.max_bases)[0])
