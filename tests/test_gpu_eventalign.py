@@ -115,3 +115,37 @@ def test_global_model_and_unaligned_rows(workload, rows_offset):
         got = rows[po[i]:po[i] + n]
         for f in binding.EVENTALIGN_DTYPE.names:
             assert np.array_equal(got[f], want[f]), (workload, i, f)
+
+
+def test_invalid_arguments_and_missing_model():
+    """A negative reference length or a zero scale is ABEA_ERR_ARG; a context without a model
+    answers ABEA_ERR_NO_MODEL (eventalign and the scaling estimate)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    b = synth.make_batch("plain_64x1kb", n_reads=2)
+    po = binding.pair_offsets(b.n_events(), np.maximum(b.n_kmers(), 1))
+    d_seq = torch.from_numpy(b.seq).to(dev)
+    d_ev = torch.from_numpy(b.events).to(dev)
+    d_res = torch.zeros(b.n * 24, dtype=torch.uint8, device=dev)
+    d_pairs = torch.zeros(int(po[-1]) * 2, dtype=torch.int32, device=dev)
+    d_pos = torch.zeros(len(b.seq), dtype=torch.int32, device=dev)
+    d_ref = torch.zeros(16, dtype=torch.uint8, device=dev)
+    d_rows = torch.zeros(int(po[-1]) * 40, dtype=torch.uint8, device=dev)
+    d_sc = torch.zeros(b.n * 3, dtype=torch.float32, device=dev)
+    d_st = torch.zeros(b.n, dtype=torch.int32, device=dev)
+    with binding.Context(0) as ctx:
+        with pytest.raises(binding.AbeaError) as ei:
+            ctx.eventalign(b.n, d_seq, b.seq_off, d_ev, b.ev_off, b.scalings, d_res, d_pairs, po, d_pos, d_ref,
+                           16, False, d_rows)
+        assert ei.value.code == binding.ABEA_ERR_NO_MODEL
+        with pytest.raises(binding.AbeaError) as ei:
+            ctx.estimate_scalings(b.n, d_seq, b.seq_off, d_ev, b.ev_off, d_sc, d_st)
+        assert ei.value.code == binding.ABEA_ERR_NO_MODEL
+        ctx.set_model(b.k, b.model_mean, b.model_stdv)
+        zero = np.array(b.scalings, np.float32)
+        zero[1, 0] = 0.0
+        for sc, ref_len in ((b.scalings, -1), (zero, 16)):
+            with pytest.raises(binding.AbeaError) as ei:
+                ctx.eventalign(b.n, d_seq, b.seq_off, d_ev, b.ev_off, sc, d_res, d_pairs, po, d_pos, d_ref,
+                               ref_len, False, d_rows)
+            assert ei.value.code == binding.ABEA_ERR_ARG

@@ -146,3 +146,25 @@ def test_integer_to_float_rounding():
     got = d_out.cpu().numpy()
     assert np.array_equal(got.view(np.uint32), v.astype(np.float32).view(np.uint32))
     assert np.array_equal(got.view(np.uint32), d_in.to(torch.float32).cpu().numpy().view(np.uint32))
+
+
+def test_invalid_arguments_are_rejected():
+    """Windows outside [2, 8], a negative or non-finite threshold, a non-finite calibration and
+    offsets that go backwards are ABEA_ERR_ARG; nothing is launched."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    raw = torch.zeros(64, dtype=torch.int16, device=dev)
+    d_ev = torch.zeros(64 * 16, dtype=torch.uint8, device=dev)
+    d_n = torch.zeros(2, dtype=torch.int32, device=dev)
+    ro = np.array([0, 30, 64], np.int64)
+    eo = np.array([0, 20, 40], np.int64)
+    cal = np.array([[0.0, 1.0], [0.0, 1.0]], np.float32)
+    bad_cal = cal.copy()
+    bad_cal[1, 1] = np.nan
+    cases = [(ro, cal, 1, 2.0), (ro, cal, 9, 2.0), (ro, cal, 3, -1.0), (ro, cal, 3, float("inf")),
+             (ro, bad_cal, 3, 2.0), (np.array([0, 40, 30], np.int64), cal, 3, 2.0)]
+    with binding.Context(0) as ctx:
+        for r_off, c, w, tau2 in cases:
+            with pytest.raises(binding.AbeaError) as ei:
+                ctx.detect_events(2, raw, r_off, c, w, tau2, d_ev, eo, d_n)
+            assert ei.value.code == binding.ABEA_ERR_ARG, (w, tau2)
