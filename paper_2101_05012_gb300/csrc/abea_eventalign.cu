@@ -116,9 +116,10 @@ static_assert(sizeof(abea_eventalign_row) == 40, "row layout");
 // Launch 2.  The grid runs over chunks of 2,048 pair slots of the whole
 // batch (the slots of read i are pair_off[i] .. pair_off[i+1]); a block takes
 // chunks in turn, each warp 256 consecutive slots of a chunk, 32 per pass.
-// Each warp forms its 32 slots' rows in its own shared-memory stage and writes the valid ones as consecutive words, so that
-// a store covers whole lines.  SMEM_MODEL: the model's (mean, stdv) table is
-// copied into shared memory once per block.
+// Each warp forms its 32 slots' rows in its own shared-memory stage and
+// writes the valid ones as consecutive words, so that a store covers whole
+// lines.  SMEM_MODEL: the model's (mean, stdv) table is copied into shared
+// memory once per block.
 template <bool SMEM_MODEL, bool WORD8>
 __global__ void __launch_bounds__(kThreads, 5) eventalign_kernel(const int64_t *meta, int32_t n, int64_t n_chunks,
                                                             int64_t seq_lo, const float *events,
