@@ -46,7 +46,7 @@ OPS_PER_CELL = 10   # FP32-pipe ops of the canonical cell: 2 FFMA, 4 FADD, 2 com
 # DRAM bytes (read + write) per band of the core kernel from one ncu capture
 # (profiles/align_kernel_bulk_reads_le15kb_sections.md), valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.
-TRAFFIC_CAPTURE = {"source_sha1": "8623d03b37fa31e644e3ce34865952eaaf6b5d56", "bytes_per_band": 85.7}
+TRAFFIC_CAPTURE = {"source_sha1": "935fb057fd3d3be84cd7d306a4a5d228c59a2281", "bytes_per_band": 85.8}
 
 
 def parse():
