@@ -49,7 +49,7 @@ struct abea_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
     size_t budget = 0;
-    size_t held = 0;            // bytes of device buffers currently allocated (excluding the model)
+    size_t held = 0;            // bytes of device buffers currently allocated from the pool
     int k = 0;
     DevBuf model, model_f;             // model rows; level mean and stdv as float2
     DevBuf rd, order, flags, kc, trace, moves, queue, offs, ev_meta, ev_bits, ea_meta, ea_ranks;
@@ -117,9 +117,11 @@ int ensure_host(HostBuf &b, size_t bytes)
     return ABEA_OK;
 }
 
-void free_dev(DevBuf &b)
+// Return a working buffer to the context's pool in stream order on st (no
+// device-wide synchronisation, unlike cudaFree).
+void free_dev(DevBuf &b, cudaStream_t st)
 {
-    if (b.p) cudaFree(b.p);
+    if (b.p) cudaFreeAsync(b.p, st);
     b.p = nullptr;
     b.cap = 0;
 }
@@ -418,12 +420,15 @@ void abea_destroy(abea_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    // wait for this context's own work only (its last batch, on whichever stream it ran), never for
+    // other contexts or other streams of the device
+    if (c->batch_done) cudaEventSynchronize(c->batch_done);
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-    cudaDeviceSynchronize();
     DevBuf *dev[] = {&c->model, &c->model_f, &c->rd, &c->order, &c->flags, &c->kc, &c->trace, &c->moves,
                      &c->queue, &c->events, &c->seq, &c->res, &c->pairs, &c->offs, &c->ev_meta, &c->ev_bits,
                      &c->ea_meta, &c->ea_ranks};
-    for (DevBuf *b : dev) free_dev(*b);
+    for (DevBuf *b : dev) free_dev(*b, c->own_stream);
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     HostBuf *host[] = {&c->h_rd, &c->h_order, &c->h_events, &c->h_seq, &c->h_res, &c->h_pairs, &c->h_offs,
                        &c->h_ev_meta, &c->h_ea_meta};
     for (HostBuf *b : host) free_host(*b);
@@ -453,30 +458,24 @@ int abea_set_model(abea_ctx *c, int k, const float *level_mean, const float *lev
         m[r].sd = (double)sd;
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
-    if (cudaStreamSynchronize(c->own_stream) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
-        return cuda_err(cudaErrorUnknown);
-    if (c->model.cap < rows * sizeof(ModelRow)) {
-        free_dev(c->model);
-        if (cudaMalloc(&c->model.p, rows * sizeof(ModelRow)) != cudaSuccess) {
-            cudaGetLastError();
-            return ABEA_ERR_NOMEM;
-        }
-        c->model.cap = rows * sizeof(ModelRow);
-    }
-    int rc = cuda_err(cudaMemcpy(c->model.p, m.data(), rows * sizeof(ModelRow), cudaMemcpyHostToDevice));
-    if (rc) return rc;
+    // The model rows may still be read by this context's last batch (on whichever stream it ran):
+    // wait for that batch only, then replace them on the context's own stream.  Nothing here waits
+    // for other contexts or streams of the device (no cudaDeviceSynchronize, no cudaFree, no copy
+    // on the legacy default stream).
+    if (cudaEventSynchronize(c->batch_done) != cudaSuccess) return cuda_err(cudaErrorUnknown);
+    cudaStream_t st = c->own_stream;
     std::vector<float2> mf(rows);
     for (size_t r = 0; r < rows; r++) mf[r] = make_float2(level_mean[r], level_stdv[r]);
-    if (c->model_f.cap < rows * sizeof(float2)) {
-        free_dev(c->model_f);
-        if (cudaMalloc(&c->model_f.p, rows * sizeof(float2)) != cudaSuccess) {
-            cudaGetLastError();
-            return ABEA_ERR_NOMEM;
-        }
-        c->model_f.cap = rows * sizeof(float2);
-    }
-    if ((rc = cuda_err(cudaMemcpy(c->model_f.p, mf.data(), rows * sizeof(float2), cudaMemcpyHostToDevice))))
+    int rc;
+    if ((rc = ensure_dev(c, c->model, rows * sizeof(ModelRow), st))) return rc;
+    if ((rc = ensure_dev(c, c->model_f, rows * sizeof(float2), st))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->model.p, m.data(), rows * sizeof(ModelRow), cudaMemcpyHostToDevice, st))))
         return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->model_f.p, mf.data(), rows * sizeof(float2), cudaMemcpyHostToDevice, st))))
+        return rc;
+    // the host copies above read m and mf, which go out of scope on return
+    if ((rc = cuda_err(cudaStreamSynchronize(st)))) return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->batch_done, st)))) return rc;
     c->k = k;
     c->h_mean.assign(level_mean, level_mean + rows);
     c->h_stdv.assign(level_stdv, level_stdv + rows);

@@ -7,8 +7,14 @@
 // cudaMalloc/cudaFree, which may synchronise the device, are not allowed.
 // Such a caller passes its inputs and outputs as before; everything else the
 // kernels need lives in one file-scope device array of fixed size
-// (kScratchBytes), which every GPU that loads the library holds until the
-// process exits.  The host side uses only static buffers as well.
+// (kScratchBytes), held on a device from the moment the library's device
+// code is loaded there until the process exits.  With CUDA's lazy module
+// loading (the default since CUDA 12.2) that moment is the first call of
+// this function on the device, whose symbol lookup loads the module: make
+// that first call before the host application fills its memory pool (or set
+// CUDA_MODULE_LOADING=EAGER, which loads it with the library).  If the
+// device has no room left for the array then, the call fails with
+// ABEA_ERR_NOMEM.  The host side uses only static buffers as well.
 //
 // Limits and sharing: the scratch holds the model rows, the per-read
 // descriptors and the kernels' working set (k-mer cache and trace, about
@@ -16,11 +22,16 @@
 // with ABEA_ERR_NOMEM before any work is issued.  Every call uses the same
 // array and leaves its contents behind; the call clears what must start at
 // zero.  Calls whose work overlaps on the GPU (two streams, or two host
-// threads) race on the array: issue them one after another on one stream.
-// The host-side static buffers make the call unsafe to enter from two host
-// threads at once.  The first call on a device looks up the array's device
-// address with cudaGetSymbolAddress (with that device current), so make that
-// first call before any stream capture.
+// threads issuing on different streams) race on the array: issue them one
+// after another on one stream.  On the host, a lock serialises the calls
+// (the static host buffers are filled under it), so entering from two host
+// threads is safe as such; only the device array is shared.  The model rows,
+// descriptors and order are copied from those pageable static buffers; CUDA
+// may stage such a copy by first synchronising with the stream, so the call
+// can wait for earlier work on its own stream (never for other streams).
+// The first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (with that device current), so make that first call
+// before any stream capture.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -56,13 +67,17 @@ std::mutex s_setup;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Device address of the scratch array on `device` (current), looked up once.
-unsigned char *scratch_for(int device)
+// On failure *no_room tells whether the device had no memory left for it.
+unsigned char *scratch_for(int device, bool *no_room)
 {
+    *no_room = false;
     std::lock_guard<std::mutex> lock(s_setup);
     if (!s_scratch[device]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) {
             cudaGetLastError();
+            *no_room = e == cudaErrorMemoryAllocation;
             return nullptr;
         }
         s_scratch[device] = (unsigned char *)p;
@@ -118,8 +133,9 @@ extern "C" int abea_align_batch_device_noalloc(int k, const float *level_mean, c
     const size_t total = align256(off_mv + mv);
     if (total > kScratchBytes) return ABEA_ERR_NOMEM;
 
-    unsigned char *base = scratch_for(device);
-    if (!base) return ABEA_ERR_CUDA;
+    bool no_room = false;
+    unsigned char *base = scratch_for(device, &no_room);
+    if (!base) return no_room ? ABEA_ERR_NOMEM : ABEA_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
     std::lock_guard<std::mutex> lock(s_setup);   // the static host buffers below are shared

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const ReadDesc *__restrict__ 
         const float *ev = events + d.ev_off;
         for (int e = threadIdx.x; e < d.n_e; e += blockDim.x) {
             const float x = ev[e];
-            if (!(fabsf(x) <= 3.0e38f)) bad = 1;     // NaN or +-inf
+            if (!isfinite(x)) bad = 1;               // NaN or +-inf (every finite event is aligned)
         }
     }
     bad = __syncthreads_or(bad);

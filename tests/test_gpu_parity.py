@@ -197,7 +197,8 @@ def test_capacity(ctx, theta):
 
 def test_extreme_events(ctx):
     # events far outside the model: the FP32 emission overflows to -inf
-    # (z^2 > 3.4e38), leaving only trim/skip paths for those cells
+    # (z^2 > 3.4e38), leaving only trim/skip paths for those cells; every
+    # finite event, up to the largest float, is aligned (no BAD_INPUT)
     rng = np.random.default_rng(4)
     base = _lengths_batch([40, 60, 90, 200, 400], seed=44)
     evs, sqs, scs = [], [], []
@@ -206,6 +207,8 @@ def test_extreme_events(ctx):
         e = e.copy()
         pos = rng.choice(len(e), max(1, len(e) // 10), replace=False)
         e[pos] = rng.choice(np.array([1e20, -1e20, 3e4, -3e4], np.float32), len(pos))
+        # finite events just below the largest float are aligned like any other event
+        e[rng.choice(len(e), 1)] = np.float32(3.2e38) if i % 2 else np.float32(-np.finfo(np.float32).max)
         evs.append(e)
         sqs.append(s)
         scs.append(c)
@@ -279,6 +282,29 @@ def test_batch_4096_ln5kb_full(ctx):
     rng = np.random.default_rng(0)
     sample = sorted(set(rng.choice(b.n, 48, replace=False).tolist()) | {int(np.argmax(b.n_events()))})
     compare(b, res, pairs, po, ids=sample)
+
+
+def test_batch_4096_ln5kb_against_fp64(ctx):
+    """The whole one-launch batch against the FP64 oracle (the accuracy
+    reference; the FP32 oracle above shares the kernel's canonical form).
+    Near-tie reads are those whose FP64 run took a decision (a traced cell's
+    three-way maximum, a band move or the end cell) by less than 1e-3.  On
+    every other read the GPU path equals the FP64 path element by element.
+    On every read the score is within 1e-4 relative of FP64, and the GPU
+    path, scored in FP64, is within 1e-3 of the FP64 optimum: where a
+    near-tie lets the paths differ, the GPU's is optimal up to the tie."""
+    from oracle import rescore
+    b = synth.make_batch("batch_4096_ln5kb")
+    res, pairs, po = run_gpu(ctx, b)
+    assert np.all(res["status"] == 0)
+    o64 = oracle.abea_batch(b, "f64", n_threads=THREADS)
+    acc = rescore.accuracy_against_fp64(b, res, pairs, po, o64)
+    print("accuracy against FP64:", acc)
+    assert acc["reads"] == b.n
+    assert acc["path_mismatch_non_tie"] == 0, acc
+    assert acc["max_rel_err_fp64"] <= 1e-4, acc
+    assert acc["max_fp64_gap_of_path"] <= 1e-3, acc
+    assert 0.0 < acc["near_tie_frac"] < 0.9, acc
 
 
 def test_wide_k9_w200_sample(ctx):

@@ -6,10 +6,11 @@ is compiled on the CPU and every pin of test_oracle_pins.py is run against it
 in a child process; at least one pin must fail (or the child must crash).
 A mutant that survives means the pins do not cover that part of the oracle.
 
-Two readings have nothing outside the oracle to pin them and are left out
-here: the parity of the band-move alternation while both band ends are -inf
-(an author comment in Alg. adaptivebandedcpu is the only source), and the
-order D > U > L among exactly equal candidates (exact floating-point ties).
+One reading has nothing outside the oracle to pin it and is left out here:
+the order D > U > L among exactly equal candidates (exact floating-point
+ties).  The parity of the band-move alternation while both band ends are -inf
+is pinned by band positions worked by hand from the author comment in
+Alg. adaptivebandedcpu (tests/golden/band_positions.json).
 """
 import os
 import subprocess
@@ -40,6 +41,7 @@ MUTANTS = [
     ("left_offset", "int32_t j_left = (kk - 1) - ll_k[b - 1];", "int32_t j_left = kk - ll_k[b - 1];"),
     ("diag_from_previous_band", "? SCORE(b - 2, j_diag)", "? SCORE(b - 1, j_diag)"),
     ("sk_rule_reversed", "advance_kmer = lower_left < upper_right;", "advance_kmer = lower_left > upper_right;"),
+    ("sk_parity_flipped", "advance_kmer = (int)(b & 1);", "advance_kmer = (int)((b & 1) ^ 1);"),
     ("trim_count", "SCORE(b, jt) = (real)(e + 1) * p.lp_trim;", "SCORE(b, jt) = (real)(e) * p.lp_trim;"),
     ("end_trim_count", "band_frame[b] + (double)(SCORE(b, j) + (real)(n_e - 1 - e) * p.lp_trim);",
      "band_frame[b] + (double)(SCORE(b, j) + (real)(n_e - e) * p.lp_trim);"),
@@ -68,6 +70,7 @@ CHILD = textwrap.dedent("""
             ("brute_force", lambda: P.pin_brute_force(lib, n_cases=40)),
             ("wide_band", lambda: P.pin_wide_band_is_full_dp(lib, n_reads=3)),
             ("invariants", lambda: P.pin_invariants(lib, n_reads=2)),
+            ("band_positions", lambda: P.pin_band_positions(lib)),
             ("fp32_long_read", lambda: P.pin_fp32_long_read(lib))]
     failed = []
     for name, fn in pins:

@@ -229,6 +229,35 @@ def test_hand_examples_f32(olib):
 
 
 # ----------------------------------------------------------------------------
+# band positions while both band ends are -inf: the alternation rule of the
+# author comment in Alg. adaptivebandedcpu (k-mer move on odd bands), worked
+# by hand for W = 8 and W = 9 (tests/golden/band_positions.json)
+
+BANDS_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "band_positions.json")
+
+
+def pin_band_positions(lib):
+    g = json.load(open(BANDS_GOLDEN))
+    rd = g["read"]
+    rng = np.random.default_rng(rd["seed"])
+    k = rd["k"]
+    mm = rng.uniform(60, 130, 4 ** k).astype(np.float32)
+    ms = rng.uniform(1, 3, 4 ** k).astype(np.float32)
+    seq = "".join(rng.choice(list("ACGT"), rd["n_bases"]))
+    ev = rng.uniform(60, 130, rd["n_events"]).astype(np.float32)
+    for case in g["cases"]:
+        for precision in ("f64", "f32"):
+            r = oracle.abea(mm, ms, k, seq, ev, (1.0, 0.0, 1.0), case["W"], precision, with_bands=True, lib=lib)
+            assert r["status"] == oracle.ST_OK
+            want = case["ll"]
+            assert r["ll"][:len(want)].tolist() == want, (case["W"], precision, r["ll"][:len(want)].tolist())
+
+
+def test_band_positions(olib):
+    pin_band_positions(olib)
+
+
+# ----------------------------------------------------------------------------
 # invariants on realistic reads; re-scoring the path from its pairs
 
 def rescore(pairs, model_mean, model_stdv, k, seq, events, sc, lib):
@@ -292,6 +321,42 @@ def pin_invariants(lib, n_reads=6):
 
 def test_invariants(olib):
     pin_invariants(olib)
+
+
+# ----------------------------------------------------------------------------
+# the vectorised FP64 path scorer (oracle/rescore.py, used by the FP64
+# accuracy checks) against the oracle's own FP64 scores and the hand examples
+
+def test_path_scores_reproduce_fp64_scores(olib):
+    from oracle import rescore
+    b = synth.make_batch("plain_64x1kb", n_reads=12)
+    o = oracle.abea_batch(b, "f64", n_threads=4, lib=olib)
+    s = rescore.path_scores(b, o["pairs"], o["pair_off"], o["n_pairs"], o["status"] == oracle.ST_OK)
+    assert np.all(o["status"] == oracle.ST_OK)
+    assert np.max(np.abs(s - o["score"]) / np.abs(o["score"])) < 1e-11
+    # a path with one pair moved off the optimum scores lower
+    p = o["pairs"].copy()
+    i = int(o["pair_off"][0]) + 5
+    p[i:i + 1, 1] = p[i + 1, 1] if p[i + 1, 1] != p[i, 1] else p[i, 1]
+    s2 = rescore.path_scores(b, p, o["pair_off"], o["n_pairs"], o["status"] == oracle.ST_OK)
+    assert s2[0] <= s[0]
+
+
+def test_path_scores_hand_examples():
+    from oracle import rescore
+    g = json.load(open(GOLDEN))
+    for ex in g["examples"]:
+        ev = np.array(ex["events"], np.float32)
+        n_e, n_k = len(ev), len(ex["seq"])
+        lp_stay = math.log(1 - 1 / (n_e / n_k + 1))
+        vals = {"E0": E0, "lp_trim": math.log(0.01), "lp_skip": math.log(1e-10), "lp_stay": lp_stay,
+                "lp_step": math.log(1 - 1e-10 - math.exp(lp_stay))}
+        want = sum(vals[t] for t in ex["terms"])
+        b = synth.custom_batch([ev], [ex["seq"].encode()], [(1.0, 0.0, 1.0)], np.asarray(g["model_levels"], np.float32),
+                               np.asarray(g["model_stdv"], np.float32), 1, 4)
+        pairs = np.asarray(ex["pairs"], np.int32)
+        s = rescore.path_scores(b, pairs, np.array([0, len(pairs)]), np.array([len(pairs)]), np.array([True]))
+        assert abs(s[0] - want) < 1e-9 * abs(want), (ex["name"], s[0], want)
 
 
 # ----------------------------------------------------------------------------
