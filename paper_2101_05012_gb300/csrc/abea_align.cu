@@ -121,6 +121,18 @@ struct Rec {
     static constexpr int R = (2 * C + 3) / 4 * 4;   // trace words per band
 };
 
+// State of a read that the lean loop never touches.  Kept per lane in shared
+// memory rather than registers, so that the lean loop's live registers fit
+// the occupancy it runs at: it is read and written only by bands run with
+// checks, by the renormalisation and at the end of the read.
+struct Cold {
+    double frame;                    // total renormalisation shift so far
+    double best;                     // best end candidate seen by this lane (unshifted)
+    long long cells;                 // in-matrix cells of bands run with checks
+    long long lean_bands;            // bands run by the lean loop (W cells each)
+    int best_e, best_le;
+};
+
 // Lane state other than the two score bands.
 template <int C>
 struct Lane {
@@ -137,11 +149,7 @@ struct Lane {
     float4 kc_cur, kc_nxt;           // prefetch window: k-mer kc_base + lane, and 32 further
     int kc_base;
     int b;                           // next band to compute
-    double frame;                    // total renormalisation shift so far
-    double best;                     // best end candidate seen by this lane (unshifted)
-    int best_e, best_le;
-    long long cells;                 // in-matrix cells of bands run with checks
-    long long lean_bands;            // bands run by the lean loop (W cells each)
+    Cold *cold;                      // the read's state the lean loop never touches
 };
 
 struct ReadCtx {
@@ -306,7 +314,7 @@ __device__ __forceinline__ void renormalise(Lane<C> &s, const ReadCtx &r, float 
             s.nb_lo = __fsub_rn(s.nb_lo, R);
             s.nb_hi = __fsub_rn(s.nb_hi, R);
         }
-        s.frame += (double)R;
+        s.cold->frame += (double)R;
     }
 }
 
@@ -443,11 +451,11 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
                 for (int i = 0; i < C; i++) {
                     if ((GROUP ? r.off0 : 0) + C * r.lane + i == jend && (!GROUP || r.lane < r.L)) {
                         const float rel = __fadd_rn(PP[i], __fmul_rn((float)(r.n_e - 1 - e), r.cs.lp_trim));
-                        const double cand = s.frame + (double)rel;
-                        if (cand > s.best) {
-                            s.best = cand;
-                            s.best_e = e;
-                            s.best_le = s.ll_e;
+                        const double cand = s.cold->frame + (double)rel;
+                        if (cand > s.cold->best) {
+                            s.cold->best = cand;
+                            s.cold->best_e = e;
+                            s.cold->best_le = s.ll_e;
                         }
                     }
                 }
@@ -455,7 +463,7 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
         }
         const int jlo = max(0, max(s.ll_e - r.n_e + 1, -s.ll_k));
         const int jhi = min(r.W, min(s.ll_e + 1, r.n_k - s.ll_k));
-        s.cells += max(0, jhi - jlo);
+        s.cold->cells += max(0, jhi - jlo);
     }
     if (GROUP) {
         float lo, hi;
@@ -488,8 +496,8 @@ __device__ __forceinline__ void swap_bands(float (&P)[C], float (&PP)[C])
 // Bands the lean loop may run from here whichever way they move: band b-1
 // and every band of the run lie wholly in the matrix and miss the end
 // column.  0 if band b-1 itself does not qualify.
-template <int C>
-__device__ __forceinline__ int lean_run(const Lane<C> &s, const ReadCtx &r)
+template <class LaneT>
+__device__ __forceinline__ int lean_run(const LaneT &s, const ReadCtx &r)
 {
     if (s.ll_e < r.W - 1 || s.ll_k < 0) return 0;
     const int re = r.n_e - 1 - s.ll_e;          // event moves before offset 0 leaves the matrix
@@ -608,7 +616,7 @@ __device__ __forceinline__ void band_loop(Lane<C> &s, const ReadCtx &r, float (&
     while (s.b <= b_end) {
         int n = lean_run(s, r);
         if (n > 0) {
-            s.lean_bands += n;
+            s.cold->lean_bands += n;
             while (n > 0) {
                 // run up to the next band with b % 64 == 0, then renormalise
                 const int to_renorm = (kRenormPeriod - (s.b % kRenormPeriod)) % kRenormPeriod + 1;
@@ -780,8 +788,308 @@ __device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lan
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-warp mode.
+//
+// The band loop is unrolled by two (the two score arrays alternate roles),
+// with one branch per band on its move; the previous band's move selects
+// the diagonal operands at run time.  A compact loop keeps the code of the
+// hot path small enough for the instruction caches (state machines over
+// more than a handful of band variants ran slower, fetch-bound, although
+// they executed fewer instructions).
+//
+// The event and k-mer operands entering the band come from two rings in
+// shared memory per warp (128 events, 128 k-mer cache entries), filled 32
+// at a time by cp.async at the start of each run of bands, so that each
+// band takes its entering operand with one shared-memory load.
+
+constexpr int kRing = 128;        // entries per operand ring
+constexpr int kRingAhead = 96;    // entries requested past the next entering one at each run start
+constexpr int kRun = 32;          // bands per run at most (the rings then never wait inside a run)
+
+struct WRings {
+    float4 k[kRing];              // k-mer cache entries (a, b, c)
+    float e[kRing];               // events
+};
+
+template <int C>
+struct WLane {
+    float X[C], A[C], B[C], Cc[C];   // operands of the lane's offsets
+    float qprev;                     // boundary value of the previous band's shifted view
+    bool kprev;                      // the last band moved by one k-mer
+    bool knext;                      // the next band moves by one k-mer (decided)
+    int ll_e, ll_k;                  // offset-0 cell of the last computed band
+    int b;                           // next band to compute
+    float xin;                       // event entering at offset 0 on the next event move
+    float4 kin;                      // k-mer operands entering at offset W'-1 on the next k-mer move
+    WRings *ring;
+    int k_req, e_req;                // ring entries requested so far (exclusive ends)
+    Cold *cold;                      // the read's state the band loop never touches
+};
+
+// Request ring entries up to kRingAhead past the next entering k-mer and
+// event (one commit group).  Entries beyond the read hold "no k-mer" and
+// +inf.  Entries consumed before the next call were requested by an earlier
+// call; the caller waits for those (wring_wait) first.
+template <int C>
+__device__ __forceinline__ void wring_refill(WLane<C> &s, const ReadCtx &r)
+{
+    const int k_next = s.ll_k + r.Wp, e_next = s.ll_e + 1;
+    while (s.k_req < k_next + kRingAhead) {
+        const int k = s.k_req + r.lane;
+        float4 *dst = s.ring->k + (k & (kRing - 1));
+        if ((unsigned)k < (unsigned)r.n_k) cp_async16(dst, r.kc + k);
+        else *dst = no_kmer();
+        s.k_req += 32;
+    }
+    while (s.e_req < e_next + kRingAhead) {
+        const int e = s.e_req + r.lane;
+        float *dst = s.ring->e + (e & (kRing - 1));
+        if ((unsigned)e < (unsigned)r.n_e) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(r.ev + e) : "memory");
+        } else {
+            *dst = pos_inf();
+        }
+        s.e_req += 32;
+    }
+    cp_async_commit();
+}
+
+// All requested ring entries have landed and are visible to the warp.
+__device__ __forceinline__ void wring_wait()
+{
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// The operands entering on the next k-mer move (k-mer ll_k + W') and event move (event ll_e + 1).
+template <int C>
+__device__ __forceinline__ void wnext_kmer(WLane<C> &s, const ReadCtx &r)
+{
+    s.kin = s.ring->k[(s.ll_k + r.Wp) & (kRing - 1)];
+}
+template <int C>
+__device__ __forceinline__ void wnext_event(WLane<C> &s)
+{
+    s.xin = s.ring->e[(s.ll_e + 1) & (kRing - 1)];
+}
+
+// Band b from S_{b-1} (P) and S_{b-2} (PP); S_b is written into PP and its
+// trace words into w.  KM: this band moves by one k-mer; s.kprev: the
+// previous band did.  FULLW: all 32 lanes are live (no lane above the band).
+template <int C, bool KM, bool FULLW>
+__device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C],
+                                           uint32_t (&w)[2 * C])
+{
+    if (KM) {
+        const float sa = __shfl_down_sync(kFull, s.A[0], 1);
+        const float sb = __shfl_down_sync(kFull, s.B[0], 1);
+        const float sc = __shfl_down_sync(kFull, s.Cc[0], 1);
+#pragma unroll
+        for (int i = 0; i < C - 1; i++) {
+            s.A[i] = s.A[i + 1];
+            s.B[i] = s.B[i + 1];
+            s.Cc[i] = s.Cc[i + 1];
+        }
+        s.A[C - 1] = r.last_lane ? s.kin.x : sa;
+        s.B[C - 1] = r.last_lane ? s.kin.y : sb;
+        s.Cc[C - 1] = r.last_lane ? s.kin.z : sc;
+    } else {
+        const float sx = __shfl_sync(kFull, s.X[C - 1], r.src_up);
+#pragma unroll
+        for (int i = C - 1; i > 0; i--) s.X[i] = s.X[i - 1];
+        s.X[0] = r.first_lane ? s.xin : sx;
+    }
+    // Q[t] = S_{b-1}[C*lane + t - 1 + KM], t = 0..C: left of slot i is Q[i], up is Q[i+1].
+    float qb;
+    if (KM) {
+        qb = __shfl_down_sync(kFull, P[0], 1);
+        if (FULLW && r.last_lane) qb = neg_inf();
+    } else {
+        qb = __shfl_sync(kFull, P[C - 1], r.src_up);
+        if (FULLW && r.first_lane) qb = neg_inf();
+    }
+    const bool kp = s.kprev;
+    float S[C];
+#pragma unroll
+    for (int i = 0; i < C; i++) {
+        const float left = KM ? P[i] : (i == 0 ? qb : P[i > 0 ? i - 1 : 0]);
+        const float up = KM ? (i == C - 1 ? qb : P[i < C - 1 ? i + 1 : 0]) : P[i];
+        // diag = the previous band's Q at t = i + KM
+        const int t = i + (KM ? 1 : 0);
+        const float d_kp = (t == C) ? s.qprev : PP[t < C ? t : 0];
+        const float d_ep = (t == 0) ? s.qprev : PP[t > 0 ? t - 1 : 0];
+        const float diag = kp ? d_kp : d_ep;
+        bool p0, p1;
+        S[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
+        if (!FULLW && i == 0) p0 = r.lane31 ? KM : p0;     // the band's move, bit 31 of word 0
+        w[2 * i] = __ballot_sync(kFull, p0);
+        w[2 * i + 1] = __ballot_sync(kFull, p1);
+    }
+#pragma unroll
+    for (int i = 0; i < C; i++) PP[i] = S[i];
+    s.qprev = qb;
+    s.kprev = KM;
+}
+
+template <int C, bool MIXED>
+__device__ __forceinline__ void wkill_dead(const ReadCtx &r, float (&S)[C])
+{
+    if (!MIXED) return;
+#pragma unroll
+    for (int i = 0; i < C; i++)
+        if (r.dead_mask & (1u << i)) S[i] = neg_inf();
+}
+
+// One band of a lean run (band b-1 and band b lie wholly in the matrix and
+// miss the end column).
+template <int C, bool MIXED, bool FULLW, bool KM>
+__device__ __forceinline__ void wlean_band(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+{
+    const int b = s.b;
+    uint32_t w[2 * C];
+    wband_fill<C, KM, FULLW>(s, r, P, PP, w);
+    wkill_dead<C, MIXED>(r, PP);
+    if (KM) s.ll_k++;
+    else s.ll_e++;
+    const float lo = __shfl_sync(kFull, PP[0], 0);
+    const float hi = far_end<C, MIXED>(r, PP);
+    s.knext = __all_sync(kFull, lo < hi);
+    store_record<C>(r, b, w);
+    if (FULLW && r.lane == 0) r.mv[b] = KM ? 1 : 0;
+    if (KM) wnext_kmer(s, r);
+    else wnext_event(s);
+    s.b = b + 1;
+}
+
+// m lean bands (m >= 1), two per iteration.  On exit P holds the last band
+// and PP the one before.
 template <int C, bool MIXED, bool FULLW>
-__device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int lane, uint32_t *bt_bufs)
+__device__ __forceinline__ void wlean_run(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C], int m)
+{
+    for (;;) {
+        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, P, PP);
+        else wlean_band<C, MIXED, FULLW, false>(s, r, P, PP);
+        if (--m == 0) {
+            swap_bands(P, PP);
+            return;
+        }
+        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, PP, P);
+        else wlean_band<C, MIXED, FULLW, false>(s, r, PP, P);
+        if (--m == 0) return;
+    }
+}
+
+// One band b = s.b with every check (trim cell, end cell, cell count, bounds of the move).
+template <int C, bool MIXED, bool FULLW>
+__device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+{
+    const int b = s.b;
+    const bool K = s.knext;
+    uint32_t w[2 * C];
+    if (K) wband_fill<C, true, FULLW>(s, r, P, PP, w);
+    else wband_fill<C, false, FULLW>(s, r, P, PP, w);
+    if (K) s.ll_k++;
+    else s.ll_e++;
+    wkill_dead<C, MIXED>(r, PP);
+    // trim state: the cell (e,-1) scores (e+1)*lp_trim
+    if (s.ll_k < 0) {
+        const int jt = -1 - s.ll_k;
+        const int e = s.ll_e - jt;
+        const float v = (e >= 0 && e < r.n_e) ? __fmul_rn((float)(e + 1), r.cs.lp_trim) : neg_inf();
+#pragma unroll
+        for (int i = 0; i < C; i++)
+            if (C * r.lane + i == jt) PP[i] = v;
+    }
+    // end cell candidates: (e, n_k-1) plus the n_e-1-e trailing events trimmed
+    const int jend = r.n_k - 1 - s.ll_k;
+    if (jend >= 0 && jend < r.W) {
+        const int e = s.ll_e - jend;
+        if (e >= 0 && e < r.n_e) {
+#pragma unroll
+            for (int i = 0; i < C; i++) {
+                if (C * r.lane + i == jend) {
+                    const float rel = __fadd_rn(PP[i], __fmul_rn((float)(r.n_e - 1 - e), r.cs.lp_trim));
+                    const double cand = s.cold->frame + (double)rel;
+                    if (cand > s.cold->best) {
+                        s.cold->best = cand;
+                        s.cold->best_e = e;
+                        s.cold->best_le = s.ll_e;
+                    }
+                }
+            }
+        }
+    }
+    const int jlo = max(0, max(s.ll_e - r.n_e + 1, -s.ll_k));
+    const int jhi = min(r.W, min(s.ll_e + 1, r.n_k - s.ll_k));
+    s.cold->cells += max(0, jhi - jlo);
+    // the move of band b+1: cells beyond the last k-mer count as -inf; both ends -inf: a k-mer
+    // move on odd bands
+    float lo = __shfl_sync(kFull, PP[0], 0);
+    float hi = far_end<C, MIXED>(r, PP);
+    if (s.ll_k >= r.n_k) lo = neg_inf();
+    if (s.ll_k + r.W - 1 >= r.n_k) hi = neg_inf();
+    const bool kn = (lo == neg_inf() && hi == neg_inf()) ? (((b + 1) & 1) != 0) : (lo < hi);
+    s.knext = __all_sync(kFull, kn);
+    store_record<C>(r, b, w);
+    if (FULLW && r.lane == 0) r.mv[b] = K ? 1 : 0;
+    if (K) wnext_kmer(s, r);
+    else wnext_event(s);
+    s.b = b + 1;
+}
+
+// Exact renormalisation after a lean band with b % 64 == 0 (see
+// renormalise): P = S_b and PP = S_{b-1}, both wholly in the matrix.
+template <int C>
+__device__ __forceinline__ void wrenormalise(WLane<C> &s, const ReadCtx &r, float (&Sb)[C], float (&Sb1)[C])
+{
+    float m = neg_inf();
+    if (r.lane < r.L) {
+#pragma unroll
+        for (int i = 0; i < C; i++)
+            if (!((r.dead_mask >> i) & 1u)) m = fmaxf(m, fmaxf(Sb[i], Sb1[i]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+    if (m <= -2048.0f) {
+        const float R = -1024.0f * floorf(__fmul_rn(-m, 1.0f / 1024.0f));
+#pragma unroll
+        for (int i = 0; i < C; i++) {
+            Sb[i] = __fsub_rn(Sb[i], R);
+            Sb1[i] = __fsub_rn(Sb1[i], R);
+        }
+        s.qprev = __fsub_rn(s.qprev, R);
+        s.cold->frame += (double)R;
+    }
+}
+
+template <int C, bool MIXED, bool FULLW>
+__device__ __forceinline__ void wband_loop(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+{
+    const int b_end = r.n_e + r.n_k;
+    while (s.b <= b_end) {
+        wring_wait();                 // the entries this run consumes were requested before
+        wring_refill(s, r);
+        const int n = min(lean_run(s, r), kRun);
+        if (n > 0) {
+            // up to the next band with b % 64 == 0, then renormalise
+            const int to_renorm = (kRenormPeriod - (s.b % kRenormPeriod)) % kRenormPeriod + 1;
+            const int m = min(n, to_renorm);
+            s.cold->lean_bands += m;
+            wlean_run<C, MIXED, FULLW>(s, r, P, PP, m);
+            if (((s.b - 1) % kRenormPeriod) == 0) wrenormalise<C>(s, r, P, PP);
+        } else {
+            wband_step<C, MIXED, FULLW>(s, r, P, PP);
+            swap_bands(P, PP);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int C, bool MIXED, bool FULLW>
+__device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int lane, uint32_t *bt_bufs,
+                           Cold &cold, WRings *rings)
 {
     ReadCtx r;
     r.ev = a.events + d.ev_off;
@@ -807,7 +1115,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     r.lsk = above ? neg_inf() : d.lp_skip;
 
     const int W = a.W, half = W / 2;
-    Lane<C> s;
+    WLane<C> s;
     float P[C], PP[C];
     // bands 0 and 1: the origin (-1,-1) at offset W/2 of band 0 (score 0);
     // band 1 = band 0 moved by one event, the trim cell (0,-1) at offset W/2.
@@ -828,29 +1136,35 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     s.qprev = __shfl_sync(kFull, PP[C - 1], r.src_up);
     if (r.first_lane) s.qprev = neg_inf();
     s.kprev = false;
-    s.ev_base = s.ll_e + 1;
-    s.ev_cur = event_value(r.ev, s.ev_base + lane, r.n_e);
-    s.ev_nxt = event_value(r.ev, s.ev_base + 32 + lane, r.n_e);
-    s.kc_base = s.ll_k + r.Wp;
-    s.kc_cur = kmer_operands(r.kc, s.kc_base + lane, r.n_k);
-    s.kc_nxt = kmer_operands(r.kc, s.kc_base + 32 + lane, r.n_k);
-    next_event(s, r, s.ll_e + 1);
-    next_kmer(s, r, s.ll_k + r.Wp);
-    s.b = 1;
-    decide_next<C, MIXED, true>(s, r, P);          // the move of band 2
+    s.ring = rings;
+    s.k_req = s.ll_k + r.Wp;
+    s.e_req = s.ll_e + 1;
+    __syncwarp();                 // the warp's previous read has finished with the rings
+    wring_refill(s, r);
+    wring_wait();
+    wnext_event(s);
+    wnext_kmer(s, r);
+    {                             // the move of band 2 from band 1 (only its trim cell can be finite)
+        float lo = __shfl_sync(kFull, P[0], 0);
+        float hi = far_end<C, MIXED>(r, P);
+        if (s.ll_k >= r.n_k) lo = neg_inf();
+        if (s.ll_k + r.W - 1 >= r.n_k) hi = neg_inf();
+        s.knext = __all_sync(kFull, (lo == neg_inf() && hi == neg_inf()) ? false : (lo < hi));
+    }
     s.b = 2;
-    s.frame = 0.0;
-    s.best = -(double)pos_inf();
-    s.best_e = INT_MAX;
-    s.best_le = 0;
-    s.cells = 0;
-    s.lean_bands = 0;
+    s.cold = &cold;
+    cold.frame = 0.0;
+    cold.best = -(double)pos_inf();
+    cold.best_e = INT_MAX;
+    cold.best_le = 0;
+    cold.cells = 0;
+    cold.lean_bands = 0;
 
-    band_loop<C, MIXED, FULLW, false>(s, r, P, PP);
+    wband_loop<C, MIXED, FULLW>(s, r, P, PP);
 
     // end cell: max score, then smallest event (the first maximum in event order)
-    double best = s.best;
-    int best_e = s.best_e, best_le = s.best_le;
+    double best = cold.best;
+    int best_e = cold.best_e, best_le = cold.best_le;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double ob = __shfl_xor_sync(kFull, best, off);
@@ -862,7 +1176,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
             best_le = ol;
         }
     }
-    const long long cells = s.cells + s.lean_bands * (long long)W;   // identical in every lane
+    const long long cells = cold.cells + cold.lean_bands * (long long)W;   // identical in every lane
 
     int status = ABEA_READ_OK;
     int n = 0;
@@ -982,17 +1296,19 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
     s.b = 1;
     s.knext = general_move<C>(s, r, (half == 0) ? d.lp_trim : neg_inf(), (half == W - 1) ? d.lp_trim : neg_inf());
     s.b = 2;
-    s.frame = 0.0;
-    s.best = -(double)pos_inf();
-    s.best_e = INT_MAX;
-    s.best_le = 0;
-    s.cells = 0;
-    s.lean_bands = 0;
+    Cold cold;
+    s.cold = &cold;
+    cold.frame = 0.0;
+    cold.best = -(double)pos_inf();
+    cold.best_e = INT_MAX;
+    cold.best_le = 0;
+    cold.cells = 0;
+    cold.lean_bands = 0;
 
     band_loop<C, false, false, true>(s, r, P, PP);
 
-    double best = s.best;
-    int best_e = s.best_e, best_le = s.best_le;
+    double best = cold.best;
+    int best_e = cold.best_e, best_le = cold.best_le;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const double ob = __shfl_xor_sync(kFull, best, off);
@@ -1022,7 +1338,7 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
             best_le = gs.best_le[g];
         }
     }
-    const long long cells = s.cells + s.lean_bands * (long long)W;
+    const long long cells = cold.cells + cold.lean_bands * (long long)W;
 
     int status = ABEA_READ_OK;
     int n = 0;
@@ -1060,8 +1376,10 @@ template <int C, int CG>
 struct Smem {
     static constexpr int RB = (CG > 0 && 2 * CG * kWarps > Rec<C>::R) ? 2 * CG * kWarps : Rec<C>::R;
     static constexpr int GS_WORDS = kWarps * 3 * kChunk * RB;
-    static constexpr size_t BYTES =
-        4 * (size_t)GS_WORDS + (CG > 0 ? (sizeof(GroupShared) + 15) / 16 * 16 : 0);
+    static constexpr size_t GS_BYTES = CG > 0 ? (sizeof(GroupShared) + 15) / 16 * 16 : 0;
+    static constexpr size_t COLD_OFF = 4 * (size_t)GS_WORDS + GS_BYTES;   // one Cold per thread
+    static constexpr size_t RING_OFF = COLD_OFF + kWarps * 32 * sizeof(Cold); // one WRings per warp
+    static constexpr size_t BYTES = RING_OFF + kWarps * sizeof(WRings);
 };
 
 // Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
@@ -1083,6 +1401,8 @@ __global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::block
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint32_t *bt = abea_smem + warp * 3 * kChunk * RB;
+    Cold &cold = reinterpret_cast<Cold *>(reinterpret_cast<char *>(abea_smem) + Smem<C, CG>::COLD_OFF)[threadIdx.x];
+    WRings *rings = reinterpret_cast<WRings *>(reinterpret_cast<char *>(abea_smem) + Smem<C, CG>::RING_OFF) + warp;
     if (CG > 0 && (int)blockIdx.x < a.n_group) {
         const int rid = a.order[blockIdx.x];
         const ReadDesc d = a.rd[rid];
@@ -1120,7 +1440,7 @@ __global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::block
             }
             continue;
         }
-        align_read<C, MIXED, FULLW>(a, d, rid, lane, bt);
+        align_read<C, MIXED, FULLW>(a, d, rid, lane, bt, cold, rings);
         __syncwarp();
     }
 }
