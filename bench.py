@@ -1,37 +1,51 @@
 #!/usr/bin/env python3
-"""Throughput of GB300-native ABEA on the one-launch batch workload.
+"""Throughput of GB300-native ABEA on the large batched workload.
 
 One step = one pass of the whole hot path (k-mer cache + input checks, band
-loop, end cell, backtrack) over the batch workload "batch_4096_ln5kb":
-4,096 synthetic reads with log-normal lengths (median 5 kb, sigma_ln 0.8,
-clipped to 500 b - 50 kb), k = 6, W = 100.  The metric is band-cell updates
-per second (GCUPS: in-matrix cells filled, summed over reads), also reported
-as reads/s.
+loop, end cell, backtrack) over the workload "large_50k_ln8kb": 50,000
+synthetic reads with log-normal lengths (median 8 kb, sigma_ln 0.5, at
+least 500 b) of which 1 % are ultra-long (log-uniform 50-200 kb), k = 6,
+W = 100; 1.35x10^11 in-matrix cells.  The metric is band-cell updates per
+second (GCUPS: in-matrix cells filled, summed over reads), also reported as
+reads/s.
 
   value : device-resident inputs (abea_align_batch_device); K steps spread
-          round-robin over D contexts, each on its own stream (D = 6 batches
-          in flight by default, so one batch's longest reads overlap the next
-          batches' work), CUDA events around all K steps.
+          round-robin over D contexts, each on its own stream (D = 2 batches
+          in flight for this workload, about 62 GB of working memory each,
+          so one batch's longest reads overlap the next batch's work), CUDA
+          events around all K steps.
   e2e   : the same metric through abea_align_packed with page-locked host
           buffers, one host thread per context; each step copies its inputs
-          host->device and its results device->host inside the timed region.
+          host->device and its results device->host inside the timed region
+          (the copies of one context overlap the other context's kernels).
 
-serving: serve_mix requests (70 % 400-base prefixes, 30 % full reads) with
-seeded Poisson arrivals at 1x and 10x the offered load of 512 channels x 450
-bases/s, through abea_server_*; p50/p99 from submission to the result in
-host memory, per class.
+Extra keys: the 4,096-read batch (median 5 kb, 6 batches in flight, and one
+batch alone: its latency) and the wide k = 9 / W = 200 model, both
+device-resident; the per-read scaling estimate, eventalign rows and event
+detection on the 4,096-read batch; serving: serve_mix requests (70 % 400-base
+prefixes, 30 % full reads) with seeded Poisson arrivals at 1x, 10x, 100x and
+1000x the offered load of 512 channels x 450 bases/s through abea_server_*,
+p50/p99 from submission to the result in host memory, per class.
 
---impl reference runs the CPU oracle (oracle/, FP32) on bounded samples of
-the same workload.  With --gpus N > 1 each rank runs its own replica of the
-workload (reads are independent; there is no data exchange).
+cpu_baseline: the CPU oracle (oracle/, -O3) on bounded, evenly spaced samples
+of the headline workload on the host cores (FP32 on all cores, FP32 on one
+thread, FP64 on all cores); the FP64 run also gives the accuracy of the GPU
+results on its sample (near-tie fraction, path mismatches on the other
+reads, score error, FP64 score of the GPU paths against the FP64 optimum).
+
+--impl reference runs the CPU oracle (FP32) on bounded samples of the same
+workload.  With --gpus N > 1 each rank runs its own replica of the workload
+(reads are independent; there is no data exchange).
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -39,20 +53,24 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "batch_4096_ln5kb"
+WORKLOAD = "large_50k_ln8kb"
+EXTRA_WORKLOADS = ("batch_4096_ln5kb", "wide_10k_ln10kb_k9_w200")
+DEPTH = {"large_50k_ln8kb": 2, "batch_4096_ln5kb": 6, "wide_10k_ln10kb_k9_w200": 2}
 METRIC = "ABEA band-cell updates/s (GCUPS) and reads/s on 1 GB300; p50/p99 latency served"
 UNIT = "GCUPS"
-OPS_PER_CELL = 10   # FP32-pipe ops of the canonical cell: 2 FFMA, 4 FADD, 2 compare, 2 select
-# DRAM bytes (read + write) per band of the core kernel from one ncu capture
-# (profiles/align_kernel_bulk_reads_le15kb_sections.md), valid only for the kernel
+# Issue slots of one cell update in the canonical form (the roofline's unit of work): 2 FFMA (emission),
+# 4 FADD, 2 compares and 2 selects (the two maxima with their directions), 2 votes (the 2-bit trace) and
+# 2 for the band's bookkeeping shared over its cells.
+OPS_PER_CELL = 14
+# DRAM bytes (read + write) per band of the core kernel from one ncu capture, valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.
-TRAFFIC_CAPTURE = {"source_sha1": "935fb057fd3d3be84cd7d306a4a5d228c59a2281", "bytes_per_band": 85.8}
+TRAFFIC_CAPTURE = {"source_sha1": None, "bytes_per_band": None}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
@@ -60,12 +78,13 @@ def parse():
     p.add_argument("--max-bases", type=int, default=None,
                    help="only the workload's reads of at most this many bases (profiling the full-load mix)")
     p.add_argument("--e2e-steps", type=int, default=None)
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target wall time of the CPU baseline sample")
+    p.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of each CPU baseline leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--depth", type=int, default=6, help="batches in flight (one context and stream each)")
+    p.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    p.add_argument("--depth", type=int, default=None, help="batches in flight (one context and stream each)")
     p.add_argument("--event-reads", type=int, default=1024, help="reads whose raw signals event detection runs on")
     p.add_argument("--serve-requests", type=int, default=500,
-                   help="serve_mix requests at 1x offered load (4x as many at 10x); 0 skips serving")
+                   help="serve_mix requests at 1x offered load (more at higher loads); 0 skips serving")
     p.add_argument("--block-theta", type=float, default=0.0,
                    help="reads above this multiple of the even per-warp share of bands run on a whole block "
                         "(<= 0: one warp per read)")
@@ -170,8 +189,10 @@ def kernel_name(W: int) -> str:
 
 def traffic_per_launch(bands: int):
     """DRAM bytes of one core-kernel launch over `bands` bands, from the ncu capture; None once the
-    kernel source differs from the captured one."""
+    kernel source differs from the captured one (or none was taken)."""
     import hashlib
+    if not TRAFFIC_CAPTURE["source_sha1"]:
+        return None
     src = os.path.join(ROOT, "paper_2101_05012_gb300", "csrc", "abea_align.cu")
     with open(src, "rb") as f:
         if hashlib.sha1(f.read()).hexdigest() != TRAFFIC_CAPTURE["source_sha1"]:
@@ -179,32 +200,52 @@ def traffic_per_launch(bands: int):
     return int(TRAFFIC_CAPTURE["bytes_per_band"] * bands)
 
 
-def oracle_rate(batch, seconds: float, threads: int):
-    """FP32 oracle on a bounded, evenly spaced sample of the batch: (GCUPS, reads/s, sample text)."""
+def make_workload_batch(synth, name, reads=None, max_bases=None):
+    workers = max(1, min(16, os.cpu_count() or 1))
+    if max_bases:
+        L = synth.read_lengths(synth.WORKLOADS[name])
+        return synth.make_batch(name, read_ids=np.nonzero(L <= max_bases)[0], workers=workers)
+    return synth.make_batch(name, n_reads=reads, workers=workers)
+
+
+def sample_ids(n: int, m: int) -> np.ndarray:
+    return np.unique(np.linspace(0, n - 1, max(1, min(n, m)), dtype=np.int64))
+
+
+def longest_first(batch, idx) -> np.ndarray:
+    """idx ordered by decreasing band count: the oracle's threads take reads in this order, one at a
+    time, so the longest ones start first and the threads finish together."""
+    idx = np.asarray(idx, dtype=np.int64)
+    bands = (batch.n_events() + batch.n_kmers())[idx]
+    return idx[np.argsort(-bands, kind="stable")]
+
+
+def oracle_rate(batch, seconds: float, threads: int, precision: str = "f32"):
+    """The oracle on a bounded, evenly spaced sample of the batch (about `seconds` of wall time on
+    `threads` threads): (GCUPS, reads/s, sample ids, results, description)."""
     from oracle import oracle
     n = batch.n
     cells_per_read = (batch.n_events() + batch.n_kmers() + 1).astype(np.float64) * batch.W
-    pilot = batch.subset(np.linspace(0, n - 1, min(n, 2 * threads), dtype=np.int64))
+    pilot = batch.subset(sample_ids(n, 2 * threads))
     t = time.perf_counter()
-    r = oracle.abea_batch(pilot, "f32", n_threads=threads)
+    r = oracle.abea_batch(pilot, precision, n_threads=threads)
     dt = max(time.perf_counter() - t, 1e-3)
     rate = r["cells"].sum() / dt
-    want_cells = rate * seconds
-    m = int(np.clip(want_cells / cells_per_read.mean(), threads, n))
-    idx = np.linspace(0, n - 1, m, dtype=np.int64)
+    m = int(np.clip(rate * seconds / cells_per_read.mean(), threads, n))
+    idx = longest_first(batch, sample_ids(n, m))
     sample = batch.subset(idx)
     t = time.perf_counter()
-    r = oracle.abea_batch(sample, "f32", n_threads=threads)
+    r = oracle.abea_batch(sample, precision, n_threads=threads)
     dt = time.perf_counter() - t
-    return (float(r["cells"].sum()) / dt / 1e9, m / dt,
-            f"{m} of {n} reads, evenly spaced ({int(r['cells'].sum())} cells), {dt:.1f} s wall")
+    desc = (f"{len(idx)} of {n} reads, evenly spaced ({int(r['cells'].sum())} cells), {precision.upper()}, "
+            f"{threads} thread{'s' if threads > 1 else ''}, {dt:.1f} s wall")
+    return float(r["cells"].sum()) / dt / 1e9, len(idx) / dt, idx, r, desc
 
 
 def serve_latency(binding, synth, device: int, load: float, n_req: int, theta: float):
     """serve_mix through the serving loop: seeded Poisson arrivals at `load` x the offered load of
     512 channels x 450 bases/s; latency from submission to the result in host memory, as the
     server stamps it."""
-    import threading
     batch, arrival, is_prefix = synth.serving_requests(n_req, load=load)
     ctx = binding.Context(device)
     ctx.set_model(batch.k, batch.model_mean, batch.model_stdv)
@@ -251,16 +292,19 @@ def serve_latency(binding, synth, device: int, load: float, n_req: int, theta: f
 
 
 def run_reference(args):
+    """The FP32 CPU oracle on the host cores: each step aligns a core-balanced, evenly spaced sample of
+    the workload (16 reads per thread, taken one at a time by the threads, longest first)."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     from paper_2101_05012_gb300 import synth
-    batch = synth.make_batch(args.workload)
+    w = synth.WORKLOADS[args.workload]
     threads = os.cpu_count() or 1
+    ids = sample_ids(w.n_reads, 16 * threads)
+    sample = synth.make_batch(w, read_ids=ids)
+    sample = sample.subset(longest_first(sample, np.arange(sample.n)))
     from oracle import oracle
     oracle.load()
-    step_reads = np.linspace(0, batch.n - 1, 64, dtype=np.int64)
-    sample = batch.subset(step_reads)
     for _ in range(args.warmup):
         oracle.abea_batch(sample, "f32", n_threads=threads)
     times, cells = [], 0
@@ -274,107 +318,190 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "reads": batch.n, "W": batch.W, "k": batch.k,
-                       "step": "FP32 CPU oracle over 64 evenly spaced reads of the workload"},
-            "reads_per_s": 64 * args.steps / total,
+            "config": {"workload": args.workload, "reads": w.n_reads, "W": w.W, "k": w.k,
+                       "step": f"FP32 CPU oracle over {len(ids)} evenly spaced reads of the workload"},
+            "reads_per_s": len(ids) * args.steps / total,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"64 of {batch.n} reads per step, {cells} cells"},
+                             "sample": f"{len(ids)} of {w.n_reads} reads per step ({cells} cells), "
+                                       f"{threads} threads taking reads one at a time, longest first"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
-    import ctypes
-    import threading
+class Workload:
+    """One workload's batch, contexts, streams and device buffers (device-resident leg)."""
 
+    def __init__(self, torch, binding, batch, dev, D, theta):
+        self.torch, self.binding, self.batch, self.dev, self.D = torch, binding, batch, dev, D
+        n = batch.n
+        self.pair_off = binding.pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
+        n_pairs = int(self.pair_off[-1])
+        self.ctxs = []
+        for _ in range(D):
+            c = binding.Context(dev.index)
+            c.set_model(batch.k, batch.model_mean, batch.model_stdv)
+            c.set_block_mode(theta)
+            self.ctxs.append(c)
+        self.d_seq = torch.from_numpy(batch.seq).to(dev)
+        self.d_ev = torch.from_numpy(batch.events).to(dev)
+        self.d_out = [torch.zeros(n * 24, dtype=torch.uint8, device=dev) for _ in range(D)]
+        self.d_pairs = [torch.zeros(max(n_pairs, 1) * 2, dtype=torch.int32, device=dev) for _ in range(D)]
+        self.streams = [torch.cuda.Stream(dev) for _ in range(D)]
+
+    def step(self, i):
+        b, j = self.batch, i % self.D
+        self.ctxs[j].align_batch_device(b.n, b.W, self.d_seq, b.seq_off, self.d_ev, b.ev_off, b.scalings,
+                                        self.d_out[j], self.d_pairs[j], self.pair_off,
+                                        stream=self.streams[j].cuda_stream)
+
+    def warm(self, warmup):
+        torch, binding = self.torch, self.binding
+        for i in range(max(warmup, self.D)):
+            self.step(i)
+        torch.cuda.synchronize(self.dev)
+        res = binding.results_from_bytes(self.d_out[0].cpu().numpy())
+        if not np.all(res["status"] == 0):
+            raise SystemExit(f"bench: {int(np.sum(res['status'] != 0))} reads failed")
+        for j in range(1, self.D):
+            if not np.array_equal(binding.results_from_bytes(self.d_out[j].cpu().numpy()), res):
+                raise SystemExit("bench: contexts disagree")
+        self.res = res
+        self.cells = int(res["cells"].sum())
+        return res
+
+    def latency(self, reps=3):
+        torch = self.torch
+        lat = []
+        for _ in range(reps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(self.streams[0])
+            self.step(0)
+            a1.record(self.streams[0])
+            a1.synchronize()
+            lat.append(a0.elapsed_time(a1))
+        return statistics.median(lat)
+
+    def timed(self, steps):
+        """ms of `steps` device-resident steps over the D streams, and the core kernels' launches and
+        summed span."""
+        torch = self.torch
+        for c in self.ctxs:
+            c.last_launch_stats()
+        main = torch.cuda.Stream(self.dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for st in self.streams:
+            st.wait_event(e0)
+        for i in range(steps):
+            self.step(i)
+        for st in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            main.wait_event(ev)
+        e1.record(main)
+        torch.cuda.synchronize(self.dev)
+        launches, align_ms = 0, 0.0
+        for c in self.ctxs:
+            nl, ms = c.last_launch_stats()
+            launches += nl
+            align_ms += ms
+        return e0.elapsed_time(e1), launches, align_ms
+
+    def e2e(self, steps, world, dist):
+        """Seconds of `steps` end-to-end steps through abea_align_packed (page-locked host buffers, one
+        host thread per context), the launches they made, the bytes copied per step and the host pairs
+        of context 0."""
+        torch, binding, b = self.torch, self.binding, self.batch
+        n = b.n
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        h_seq, h_ev = pin(b.seq), pin(b.events)
+        n_pairs = int(self.pair_off[-1])
+        h_out = [torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy() for _ in range(self.D)]
+        h_pairs = [torch.zeros(max(n_pairs, 1) * 2, dtype=torch.int32).pin_memory().numpy() for _ in range(self.D)]
+        sc = np.ascontiguousarray(b.scalings, np.float32)
+        errors = []
+
+        def e2e_step(j):
+            c = self.ctxs[j]
+            rc = c.lib.abea_align_packed(c.h, n, b.W, binding._p(h_seq), binding._p(b.seq_off), binding._p(h_ev),
+                                         binding._p(b.ev_off), binding._p(sc), binding._p(h_out[j]),
+                                         binding._p(h_pairs[j]), binding._p(self.pair_off),
+                                         ctypes.c_void_p(self.streams[j].cuda_stream))
+            if rc != 0:
+                errors.append(rc)
+
+        for j in range(self.D):
+            e2e_step(j)
+        for c in self.ctxs:
+            c.last_launch_stats()
+        gate = threading.Barrier(self.D + 1)
+
+        def worker(j):
+            gate.wait()
+            for _ in range(j, steps, self.D):
+                e2e_step(j)
+
+        threads = [threading.Thread(target=worker, args=(j,)) for j in range(self.D)]
+        for th in threads:
+            th.start()
+        if world > 1:
+            dist.barrier()
+        gate.wait()
+        t = time.perf_counter()
+        for th in threads:
+            th.join()
+        secs = time.perf_counter() - t
+        if errors:
+            raise binding.AbeaError(errors[0], "abea_align_packed")
+        launches = sum(c.last_launch_stats()[0] for c in self.ctxs)
+        for j in range(self.D):
+            if not np.array_equal(binding.results_from_bytes(h_out[j]), self.res):
+                raise SystemExit("bench: host-memory results differ from device-resident results")
+        h2d = int(b.seq.nbytes + b.events.nbytes + n * (112 + 4))
+        d2h = int(n * 24 + n_pairs * 8)
+        return secs, launches, h2d, d2h, h_pairs[0].reshape(-1, 2)
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+        self.ctxs = []
+        self.d_seq = self.d_ev = self.d_out = self.d_pairs = None
+        self.torch.cuda.synchronize(self.dev)
+        self.torch.cuda.empty_cache()
+
+
+def run_ours(args):
     import torch
     import torch.distributed as dist
 
     from paper_2101_05012_gb300 import binding, synth
 
     rank, local_rank, world = dist_env()
+    # synthetic inputs first (a process pool, started before any CUDA call)
+    batch = make_workload_batch(synth, args.workload, args.reads, args.max_bases)
+    extra_batches = {}
+    if not args.no_extra and rank == 0 and world == 1 and not args.reads and not args.max_bases:
+        for name in EXTRA_WORKLOADS:
+            if name != args.workload:
+                extra_batches[name] = make_workload_batch(synth, name)
     torch.cuda.set_device(local_rank)            # before the process group: NCCL binds the current device
     dev = torch.device("cuda", local_rank)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    if args.max_bases:
-        L = synth.read_lengths(synth.WORKLOADS[args.workload])
-        batch = synth.make_batch(args.workload, read_ids=np.nonzero(L <= args.max_bases)[0])
-    else:
-        batch = synth.make_batch(args.workload, n_reads=args.reads)
     n = batch.n
-    D = max(1, args.depth)
-    pair_off = binding.pair_offsets(batch.n_events(), np.maximum(batch.n_kmers(), 1))
-    n_pairs = int(pair_off[-1])
+    D = args.depth or DEPTH.get(args.workload, 2)
+    wl = Workload(torch, binding, batch, dev, D, args.block_theta)
+    wl.warm(args.warmup)
+    cells = wl.cells
+    lat = wl.latency()
 
-    # D contexts, each with its own stream and outputs; step i runs on context i % D, so up to D
-    # batches are in flight and one batch's last long reads overlap the next batches' work
-    ctxs = []
-    for _ in range(D):
-        c = binding.Context(local_rank)
-        c.set_model(batch.k, batch.model_mean, batch.model_stdv)
-        c.set_block_mode(args.block_theta)
-        ctxs.append(c)
-    d_seq = torch.from_numpy(batch.seq).to(dev)
-    d_ev = torch.from_numpy(batch.events).to(dev)
-    d_out = [torch.zeros(n * 24, dtype=torch.uint8, device=dev) for _ in range(D)]
-    d_pairs = [torch.zeros(n_pairs * 2, dtype=torch.int32, device=dev) for _ in range(D)]
-    streams = [torch.cuda.Stream(dev) for _ in range(D)]
-    main = torch.cuda.Stream(dev)
-
-    def step(i):
-        j = i % D
-        ctxs[j].align_batch_device(n, batch.W, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out[j],
-                                   d_pairs[j], pair_off, stream=streams[j].cuda_stream)
-
-    for i in range(max(args.warmup, D)):
-        step(i)
-    torch.cuda.synchronize(dev)
-    res = binding.results_from_bytes(d_out[0].cpu().numpy())
-    if not np.all(res["status"] == 0):
-        raise SystemExit(f"bench: {int(np.sum(res['status'] != 0))} reads failed")
-    for j in range(1, D):
-        if not np.array_equal(binding.results_from_bytes(d_out[j].cpu().numpy()), res):
-            raise SystemExit("bench: contexts disagree")
-    cells = int(res["cells"].sum())
-
-    # one batch at a time (latency of a batch; not the headline)
-    lat = []
-    for _ in range(3):
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(streams[0])
-        step(0)
-        a1.record(streams[0])
-        a1.synchronize()
-        lat.append(a0.elapsed_time(a1))
-    for c in ctxs:
-        c.last_launch_stats()                    # reset the launch counters
-
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local_rank)
-    e0.record(main)
-    for st in streams:
-        st.wait_event(e0)
-    for i in range(args.steps):
-        step(i)
-    for st in streams:
-        ev = torch.cuda.Event()
-        ev.record(st)
-        main.wait_event(ev)
-    e1.record(main)
-    torch.cuda.synchronize(dev)
+    ms_total, launches, align_ms = wl.timed(args.steps)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    launches, align_ms = 0, 0.0
-    for c in ctxs:
-        nl, ms = c.last_launch_stats()
-        launches += nl
-        align_ms += ms
     if world > 1:
         dist.barrier()
     ms_total = max_over_ranks(ms_total, world, dist, dev)
@@ -382,60 +509,15 @@ def run_ours(args):
     value = job_rate(cells, args.steps, ms_total / 1e3, world) / 1e9
     reads_per_s = job_rate(n, args.steps, ms_total / 1e3, world)
 
-    # end to end through the host-memory call (abea_align_packed, page-locked host buffers): one host
-    # thread per context, each call copies its inputs in and its results out
-    e2e_steps = args.e2e_steps or max(3, min(args.steps, 60))
-    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-    h_seq, h_ev = pin(batch.seq), pin(batch.events)
-    h_out = [torch.zeros(n * 24, dtype=torch.uint8).pin_memory().numpy() for _ in range(D)]
-    h_pairs = [torch.zeros(n_pairs * 2, dtype=torch.int32).pin_memory().numpy() for _ in range(D)]
-    sc = np.ascontiguousarray(batch.scalings, np.float32)
-    errors = []
-
-    def e2e_step(j):
-        c = ctxs[j]
-        rc = c.lib.abea_align_packed(c.h, n, batch.W, binding._p(h_seq), binding._p(batch.seq_off),
-                                     binding._p(h_ev), binding._p(batch.ev_off), binding._p(sc),
-                                     binding._p(h_out[j]), binding._p(h_pairs[j]), binding._p(pair_off),
-                                     ctypes.c_void_p(streams[j].cuda_stream))
-        if rc != 0:
-            errors.append(rc)
-
-    for j in range(D):
-        e2e_step(j)
-    for c in ctxs:
-        c.last_launch_stats()
-    gate = threading.Barrier(D + 1)
-
-    def worker(j):
-        gate.wait()
-        for _ in range(j, e2e_steps, D):
-            e2e_step(j)
-
-    threads = [threading.Thread(target=worker, args=(j,)) for j in range(D)]
-    for th in threads:
-        th.start()
-    if world > 1:
-        dist.barrier()
-    gate.wait()
-    t = time.perf_counter()
-    for th in threads:
-        th.join()
-    e2e_s = time.perf_counter() - t
-    if errors:
-        raise binding.AbeaError(errors[0], "abea_align_packed")
-    e2e_launches = sum(c.last_launch_stats()[0] for c in ctxs)
+    # end to end through the host-memory call
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10 if n > 10_000 else 60))
+    e2e_s, e2e_launches, h2d, d2h, h_pairs = wl.e2e(e2e_steps, world, dist)
     e2e_s = max_over_ranks(e2e_s, world, dist, dev)
-    for j in range(D):
-        if not np.array_equal(binding.results_from_bytes(h_out[j]), res):
-            raise SystemExit("bench: host-memory results differ from device-resident results")
     e2e_value = job_rate(cells, e2e_steps, e2e_s, world) / 1e9
-    h2d = int(batch.seq.nbytes + batch.events.nbytes + n * (112 + 4))
-    d2h = int(n * 24 + (pair_off[-1] - pair_off[0]) * 8)
 
-    # roofline of the core kernel (98 % of device time): FP32-pipe issue.  With D batches in flight
-    # the launches overlap; the kernel's rate is the cells of one launch over the launch period
-    # (timed region / launches); the mean span of a single launch is reported beside it.
+    # roofline of the core kernel: FP32-pipe issue.  With D batches in flight the launches overlap;
+    # the kernel's rate is the cells of one launch over the launch period (timed region / launches);
+    # the mean span of a single launch is reported beside it.
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = measured_peaks()
@@ -447,43 +529,109 @@ def run_ours(args):
     bands = int((batch.n_events() + batch.n_kmers() + 1).sum())
     trace_bytes = bands * 4 * record_words(batch.W)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
-                "traffic": traffic_per_launch(bands),
-                "kernel": kernel_name(batch.W), "launch_period_ms": period_ms,
-                "launch_span_ms": span_ms, "batches_in_flight": D,
+                "traffic": traffic_per_launch(bands), "kernel": kernel_name(batch.W),
+                "launch_period_ms": period_ms, "launch_span_ms": span_ms, "batches_in_flight": D,
                 "ops_per_cell": OPS_PER_CELL,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)"}
     if clk and clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
+    config = {"workload": args.workload, "reads": n, "W": batch.W, "k": batch.k, "cells_per_step": cells,
+              "bases_per_step": int(batch.seq.size), "events_per_step": int(batch.events.size),
+              "parallelism": f"replicas x{world}" if world > 1 else "1 GPU", "batches_in_flight": D,
+              "block_theta": args.block_theta,
+              "l2": f"inputs ({batch.events.nbytes / 1e9:.1f} GB events) and the trace "
+                    f"({trace_bytes / 1e9:.1f} GB per step) exceed the 129 MB L2"}
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
+           "host_threads": D}
+    h_res, h_pair_off = wl.res, wl.pair_off
+    wl.close()
 
-    # the per-read scaling estimate (method of moments) over the same batch, device-resident: a
-    # bandwidth-bound pass (4 B per event, 1 B per base, the model rows from L2)
+    # extra workloads (device-resident rate; the 4,096-read batch also alone, and the secondary kernels)
+    extra, scal_line, ea_line, ev_line = {}, None, None, None
+    for name, xb in extra_batches.items():
+        xD = DEPTH.get(name, 2)
+        x = Workload(torch, binding, xb, dev, xD, args.block_theta)
+        x.warm(args.warmup)
+        xlat = x.latency()
+        xsteps = max(6, min(args.steps, 30 if xb.n <= 4096 else 10))
+        xms, xl, _ = x.timed(xsteps)
+        extra[name] = {"value": x.cells * xsteps / (xms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": xms / xsteps,
+                       "steps": xsteps, "batches_in_flight": xD, "batch_latency_ms": xlat, "reads": xb.n,
+                       "W": xb.W, "k": xb.k, "cells_per_step": x.cells, "gpu_launches": xl,
+                       "kernel": kernel_name(xb.W)}
+        if name == "batch_4096_ln5kb":
+            scal_line, ea_line, ev_line = secondary_kernels(torch, binding, synth, x, args)
+        x.close()
+
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = [serve_latency(binding, synth, local_rank, load, n_req, 1.0)
+                   for load, n_req in ((1.0, args.serve_requests), (10.0, 4 * args.serve_requests),
+                                       (100.0, 8 * args.serve_requests), (1000.0, 8 * args.serve_requests))]
+
+    cpu, accuracy = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import rescore
+        threads_n = os.cpu_count() or 1
+        gc, rps, _, _, desc = oracle_rate(batch, args.cpu_seconds, threads_n, "f32")
+        g1, r1, _, _, d1 = oracle_rate(batch, args.cpu_seconds, 1, "f32")
+        g64, r64, idx64, o64, d64 = oracle_rate(batch, args.cpu_seconds, threads_n, "f64")
+        sub = batch.subset(idx64)
+        gp = [h_pairs[h_pair_off[i]:h_pair_off[i] + h_res["n_pairs"][i]] for i in idx64]
+        sub_off = np.zeros(len(idx64) + 1, np.int64)
+        np.cumsum([len(p) for p in gp], out=sub_off[1:])
+        gpairs = np.concatenate(gp) if gp else np.zeros((0, 2), np.int32)
+        accuracy = rescore.accuracy_against_fp64(sub, h_res[idx64], gpairs, sub_off, o64)
+        accuracy["sample"] = f"the FP64 leg's {len(idx64)} reads"
+        cpu = {"value": gc, "unit": UNIT, "cores": threads_n, "kind": "oracle", "sample": desc,
+               "reads_per_s": rps, "flags": "gcc -O3 -ffp-contract=off",
+               "threads_1": {"value": g1, "unit": UNIT, "reads_per_s": r1, "sample": d1},
+               "fp64": {"value": g64, "unit": UNIT, "reads_per_s": r64, "sample": d64}}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "reads_per_s": reads_per_s, "batch_latency_ms": lat, "kernel_launch_span_ms": span_ms,
+                "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "accuracy": accuracy, "clocks": clk, "extra_workloads": extra, "serving": serving,
+                "scalings_estimate": scal_line, "event_detection": ev_line, "eventalign": ea_line}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def secondary_kernels(torch, binding, synth, x, args):
+    """The per-read scaling estimate, eventalign rows and event detection over the 4,096-read batch
+    (context 0 of workload x, after its timed run)."""
+    batch, dev, n = x.batch, x.dev, x.batch.n
+    ctx, st = x.ctxs[0], x.streams[0]
+    steps = max(6, min(args.steps, 30))
+    hbm = float(measured_peaks().get("hbm_gbs") or 6800.0)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(st)
+        for _ in range(steps):
+            fn()
+        s1.record(st)
+        s1.synchronize()
+        return s0.elapsed_time(s1) / steps
+
     d_sc = torch.zeros(n * 3, dtype=torch.float32, device=dev)
     d_sst = torch.zeros(n, dtype=torch.int32, device=dev)
-
-    def scal():
-        ctxs[0].estimate_scalings(n, d_seq, batch.seq_off, d_ev, batch.ev_off, d_sc, d_sst,
-                                  stream=streams[0].cuda_stream)
-
-    for _ in range(3):
-        scal()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(streams[0])
-    for _ in range(args.steps):
-        scal()
-    s1.record(streams[0])
-    s1.synchronize()
-    scal_ms = s0.elapsed_time(s1) / args.steps
+    scal_ms = timed(lambda: ctx.estimate_scalings(n, x.d_seq, batch.seq_off, x.d_ev, batch.ev_off, d_sc, d_sst,
+                                                  stream=st.cuda_stream))
     scal_bytes = int(batch.events.nbytes + batch.seq.nbytes)
-    hbm = float(measured_peaks().get("hbm_gbs") or 6800.0)
-    scalings_line = {"kernel": "scalings_kernel", "ms_per_launch": scal_ms, "reads_per_s": n / (scal_ms / 1e3),
-                     "roofline": {"bound": "hbm", "achieved": scal_bytes / (scal_ms / 1e3) / 1e9,
-                                  "peak": hbm, "unit": "GB/s",
-                                  "frac": scal_bytes / (scal_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": scal_bytes},
-                     "ok_reads": int((d_sst == 0).sum().item())}
+    scal = {"kernel": "scalings_kernel", "ms_per_launch": scal_ms, "reads_per_s": n / (scal_ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": scal_bytes / (scal_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": scal_bytes / (scal_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": scal_bytes},
+            "ok_reads": int((d_sst == 0).sum().item())}
 
-    # eventalign rows over the batch's alignments (context 0's results and pairs), each read mapped to a
-    # reference with 3 % indels: a gather pass, 8 B of pair + 4 B of event + 4 B of reference position in,
-    # 40 B of record out per pair
     ea_refs, ea_pos, ea_base = [], np.zeros(len(batch.seq), np.int32), 0
     for i in range(n):
         r_, p_ = synth.make_ref_alignment(batch.seq[batch.seq_off[i]:batch.seq_off[i + 1]].tobytes(), 9, i)
@@ -492,101 +640,38 @@ def run_ours(args):
         ea_base += len(r_)
     d_ref = torch.from_numpy(np.concatenate(ea_refs)).to(dev)
     d_rpos = torch.from_numpy(ea_pos).to(dev)
-    d_rows = torch.empty(n_pairs * 40, dtype=torch.uint8, device=dev)
-
-    def eventalign():
-        ctxs[0].eventalign(n, d_seq, batch.seq_off, d_ev, batch.ev_off, batch.scalings, d_out[0], d_pairs[0],
-                           pair_off, d_rpos, d_ref, ea_base, False, d_rows, stream=streams[0].cuda_stream)
-
-    for _ in range(3):
-        eventalign()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(streams[0])
-    for _ in range(args.steps):
-        eventalign()
-    a1.record(streams[0])
-    a1.synchronize()
-    ea_ms = a0.elapsed_time(a1) / args.steps
-    rows_n = int(res["n_pairs"].sum())
+    d_rows = torch.empty(int(x.pair_off[-1]) * 40, dtype=torch.uint8, device=dev)
+    ea_ms = timed(lambda: ctx.eventalign(n, x.d_seq, batch.seq_off, x.d_ev, batch.ev_off, batch.scalings, x.d_out[0],
+                                         x.d_pairs[0], x.pair_off, d_rpos, d_ref, ea_base, False, d_rows,
+                                         stream=st.cuda_stream))
+    rows_n = int(x.res["n_pairs"].sum())
     ea_bytes = rows_n * (8 + 4 + 4 + 40)
-    eventalign_line = {"kernels": ["eventalign_ranks_kernel", "eventalign_kernel"], "rows": rows_n,
-                       "ms_per_call": ea_ms, "launches_per_call": 2, "rows_per_s": rows_n / (ea_ms / 1e3),
-                       "roofline": {"bound": "hbm", "achieved": ea_bytes / (ea_ms / 1e3) / 1e9, "peak": hbm,
-                                    "unit": "GB/s", "frac": ea_bytes / (ea_ms / 1e3) / 1e9 / hbm,
-                                    "bytes_per_launch": ea_bytes}}
+    ea = {"kernels": ["eventalign_ranks_kernel", "eventalign_kernel"], "rows": rows_n, "ms_per_call": ea_ms,
+          "launches_per_call": 2, "rows_per_s": rows_n / (ea_ms / 1e3),
+          "roofline": {"bound": "hbm", "achieved": ea_bytes / (ea_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": ea_bytes / (ea_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": ea_bytes}}
     del d_ref, d_rpos, d_rows
 
-    # event detection over the raw signals of the first 1,024 reads (about 9 samples per base,
-    # int16): three launches over tiles of 4,096 samples of all reads; algorithmic bytes = the
-    # samples read once and the events written once
-    events_line = None
+    ev = None
     if args.event_reads > 0:
-        rb = synth.make_raw_batch(args.workload, n_reads=min(args.event_reads, synth.WORKLOADS[args.workload].n_reads))
+        rb = synth.make_raw_batch("batch_4096_ln5kb", n_reads=min(args.event_reads, n))
         d_raw = torch.from_numpy(rb.raw).to(dev)
         ev_cap = (rb.raw_off[1:] - rb.raw_off[:-1]) // 3 + 2
         ev_off = np.zeros(rb.n + 1, np.int64)
         np.cumsum(ev_cap, out=ev_off[1:])
         d_evs = torch.zeros(int(ev_off[-1]) * 16, dtype=torch.uint8, device=dev)
         d_nev = torch.zeros(rb.n, dtype=torch.int32, device=dev)
-
-        def detect():
-            ctxs[0].detect_events(rb.n, d_raw, rb.raw_off, rb.calib, 3, 2.0, d_evs, ev_off, d_nev,
-                                  stream=streams[0].cuda_stream)
-
-        for _ in range(3):
-            detect()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record(streams[0])
-        for _ in range(args.steps):
-            detect()
-        q1.record(streams[0])
-        q1.synchronize()
-        det_ms = q0.elapsed_time(q1) / args.steps
+        det_ms = timed(lambda: ctx.detect_events(rb.n, d_raw, rb.raw_off, rb.calib, 3, 2.0, d_evs, ev_off, d_nev,
+                                                 stream=st.cuda_stream))
         n_events = int(d_nev.sum().item())
         det_bytes = int(rb.raw.nbytes + n_events * 16)
-        events_line = {"kernels": ["event_tiles_kernel<3>", "event_scan_kernel", "event_emit_kernel"],
-                       "reads": rb.n, "samples": int(rb.raw.size), "events": n_events,
-                       "ms_per_call": det_ms, "launches_per_call": 3, "samples_per_s": rb.raw.size / (det_ms / 1e3),
-                       "roofline": {"bound": "hbm", "achieved": det_bytes / (det_ms / 1e3) / 1e9, "peak": hbm,
-                                    "unit": "GB/s", "frac": det_bytes / (det_ms / 1e3) / 1e9 / hbm,
-                                    "bytes_per_launch": det_bytes}}
+        ev = {"kernels": ["event_tiles_kernel<3>", "event_scan_kernel", "event_emit_kernel"], "reads": rb.n,
+              "samples": int(rb.raw.size), "events": n_events, "ms_per_call": det_ms, "launches_per_call": 3,
+              "samples_per_s": rb.raw.size / (det_ms / 1e3),
+              "roofline": {"bound": "hbm", "achieved": det_bytes / (det_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": det_bytes / (det_ms / 1e3) / 1e9 / hbm, "bytes_per_launch": det_bytes}}
         del d_raw, d_evs
-
-    serving = None
-    if rank == 0 and world == 1 and args.serve_requests > 0:
-        serving = [serve_latency(binding, synth, local_rank, load, n_req, 1.0)
-                   for load, n_req in ((1.0, args.serve_requests), (10.0, 4 * args.serve_requests))]
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads_n = os.cpu_count() or 1
-        gc, rps, desc = oracle_rate(batch, args.cpu_seconds, threads_n)
-        cpu = {"value": gc, "unit": UNIT, "cores": threads_n, "kind": "oracle", "sample": desc, "reads_per_s": rps}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "reads": n, "W": batch.W, "k": batch.k,
-                           "cells_per_step": cells, "bases_per_step": int(batch.seq.size),
-                           "events_per_step": int(batch.events.size),
-                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                           "batches_in_flight": D, "block_theta": args.block_theta,
-                           "l2": f"inputs ({batch.events.nbytes / 1e6:.0f} MB events) and the trace "
-                                 f"({trace_bytes / 1e9:.1f} GB per step) exceed the 129 MB L2"},
-                "reads_per_s": reads_per_s, "batch_latency_ms": statistics.median(lat),
-                "kernel_launch_span_ms": span_ms, "gpu_launches": launches,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps, "gpu_launches": e2e_launches,
-                        "host_threads": D},
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "serving": serving,
-                "scalings_estimate": scalings_line, "event_detection": events_line, "eventalign": eventalign_line}
-        print(json.dumps(line), flush=True)
-    for c in ctxs:
-        c.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    return scal, ea, ev
 
 
 def main():

@@ -5,7 +5,10 @@ CPU-baseline leg of bench.py.  The product path (the CUDA library and its
 binding) never imports this module.
 
 `build()` compiles abea_oracle.c twice (FP64, and FP32 with -DORACLE_F32)
-with -ffp-contract=off into oracle/_build/liboracle.so.
+with -O3 -ffp-contract=off into oracle/_build/liboracle.so (no fused
+multiply-add unless written as fma(), no reassociation: the results do not
+depend on the optimisation level or the host; no -march=native, so the same
+source gives the same code paths on the x86 and Arm hosts).
 """
 from __future__ import annotations
 
@@ -34,7 +37,7 @@ class OracleResult(ctypes.Structure):
 def build(src: str = SRC, out: str = LIB, extra_flags=()) -> str:
     """Compile the oracle (both precisions) into a shared library; returns its path."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-std=c11", "-D_POSIX_C_SOURCE=200809L", *extra_flags]
+    base = ["gcc", "-O3", "-ffp-contract=off", "-fPIC", "-std=c11", "-D_POSIX_C_SOURCE=200809L", *extra_flags]
     o64 = out + ".f64.o"
     o32 = out + ".f32.o"
     subprocess.run(base + ["-c", src, "-o", o64], check=True)
@@ -75,7 +78,9 @@ def load(path: Optional[str] = None):
         if path is not None:
             return _setup(ctypes.CDLL(path))
         if _lib is None:
-            if not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+            here = os.path.abspath(__file__)
+            if (not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC)
+                    or os.path.getmtime(LIB) < os.path.getmtime(here)):
                 build()
             _lib = _setup(ctypes.CDLL(LIB))
         return _lib

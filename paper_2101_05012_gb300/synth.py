@@ -263,24 +263,51 @@ def make_read(w: Workload, r: int, L: int, model_mean, model_stdv, dwell_mean=No
     return seq, ev, np.array([scale, shift, var], dtype=np.float32)
 
 
-def make_batch(w, n_reads: Optional[int] = None, read_ids=None) -> Batch:
-    """Generate a workload (or the first n_reads / the listed reads of it)."""
+def _make_reads(w: Workload, ids, L, mm, ms):
+    """Packed bases, base counts, events, event counts and scalings of reads `ids`."""
+    seqs, evs, scs = [], [], []
+    for r in ids:
+        s, e, sc = make_read(w, int(r), int(L[r]), mm, ms)
+        seqs.append(s)
+        evs.append(e)
+        scs.append(sc)
+    return (np.concatenate(seqs) if seqs else np.zeros(0, np.uint8), np.array([len(s) for s in seqs], np.int64),
+            np.concatenate(evs) if evs else np.zeros(0, np.float32), np.array([len(e) for e in evs], np.int64),
+            np.stack(scs) if scs else np.zeros((0, 3), np.float32))
+
+
+def _make_reads_job(args):
+    w, ids = args
+    mm, ms = make_model(w.k, w.seed, w.level_mean_range, w.level_stdv_range)
+    return _make_reads(w, ids, read_lengths(w), mm, ms)
+
+
+def make_batch(w, n_reads: Optional[int] = None, read_ids=None, workers: int = 1) -> Batch:
+    """Generate a workload (or the first n_reads / the listed reads of it).
+
+    With workers > 1 the reads are generated in that many processes (started
+    with "spawn", so the caller may already use CUDA); every read is drawn
+    from its own counter-based streams, so the batch is the same either way.
+    """
     if isinstance(w, str):
         w = WORKLOADS[w]
     mm, ms = make_model(w.k, w.seed, w.level_mean_range, w.level_stdv_range)
     L = read_lengths(w)
     if read_ids is None:
         read_ids = range(w.n_reads if n_reads is None else min(n_reads, w.n_reads))
-    seqs, evs, scs = [], [], []
-    for r in read_ids:
-        s, e, sc = make_read(w, int(r), int(L[r]), mm, ms)
-        seqs.append(s)
-        evs.append(e)
-        scs.append(sc)
-    return Batch(w.k, w.W, mm, ms,
-                 np.concatenate(seqs) if seqs else np.zeros(0, np.uint8), _offsets([len(s) for s in seqs]),
-                 np.concatenate(evs) if evs else np.zeros(0, np.float32), _offsets([len(e) for e in evs]),
-                 np.stack(scs) if scs else np.zeros((0, 3), np.float32), w.name)
+    ids = np.asarray(list(read_ids), dtype=np.int64)
+    if workers > 1 and len(ids) > 4 * workers:
+        import multiprocessing as mp
+        chunks = [c for c in np.array_split(ids, 4 * workers) if len(c)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_make_reads_job, [(w, c) for c in chunks])
+    else:
+        parts = [_make_reads(w, ids, L, mm, ms)]
+    seq = np.concatenate([p[0] for p in parts])
+    events = np.concatenate([p[2] for p in parts])
+    return Batch(w.k, w.W, mm, ms, seq, _offsets(np.concatenate([p[1] for p in parts])),
+                 events, _offsets(np.concatenate([p[3] for p in parts])),
+                 np.concatenate([p[4] for p in parts]).reshape(-1, 3), w.name)
 
 
 def serving_requests(n_requests: int, load: float = 1.0, w: Optional[Workload] = None,

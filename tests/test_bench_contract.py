@@ -29,7 +29,7 @@ def test_reference_arm_line():
         assert key in d, key
     assert d["unit"] == "GCUPS" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
-    assert d["config"]["workload"] == "batch_4096_ln5kb"
+    assert d["config"]["workload"] == "large_50k_ln8kb"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
