@@ -178,6 +178,57 @@ int abea_eventalign(abea_ctx *ctx, int32_t n, const uint8_t *d_seq, const int64_
                     const int32_t *d_ref_pos, const uint8_t *d_ref, int64_t ref_len, int scale_events,
                     abea_eventalign_row *d_rows, void *cuda_stream);
 
+/* Per-read summary of an alignment, for eventalign's consumers (f5c's
+ * eventalign lists a --summary option, "summarise the alignment of each
+ * read", with no format; the fields below are a reading).  From a read's
+ * result and its pairs (event e, k-mer j), ascending:
+ *   first_event, last_event  events of the first and last pair (-1 if none);
+ *                            the first_event leading and n_events-1-last_event
+ *                            trailing events are trimmed;
+ *   stays    pairs whose event follows the previous pair's on the same k-mer
+ *            (e+1, j): an extra event on one k-mer;
+ *   skips    pairs whose k-mer follows the previous pair's with the same
+ *            event (e, j+1): a k-mer entered without an event of its own;
+ *   events_aligned = n_pairs - skips (distinct events in the pairs);
+ *   score_per_event = score / n_events;
+ *   flags: ABEA_QC_NOT_ALIGNED (status is not ABEA_READ_OK), ABEA_QC_TRIMMED
+ *   (more than half of the events trimmed), ABEA_QC_SKIPS (skips above a fifth
+ *   of the k-mers), ABEA_QC_LOW_SCORE (score_per_event below -10). */
+#define ABEA_QC_NOT_ALIGNED 1
+#define ABEA_QC_TRIMMED 2
+#define ABEA_QC_SKIPS 4
+#define ABEA_QC_LOW_SCORE 8
+typedef struct {
+    int32_t read, status, n_events, n_kmers, n_pairs;
+    int32_t first_event, last_event, events_aligned, stays, skips;
+    float score, score_per_event;
+    int32_t flags;
+} abea_read_summary;
+/* Summaries of reads 0..n-1 from the device results and pairs of
+ * abea_align_batch_device (d_results, d_pairs at 2*pair_off[i]); ev_off,
+ * seq_off and pair_off are host arrays, k the model's k (n_kmers = bases - k
+ * + 1); d_out: n device records.  Enqueued on cuda_stream (one warp per
+ * read). */
+int abea_summarise(abea_ctx *ctx, int32_t n, const int64_t *seq_off, const int64_t *ev_off,
+                   const abea_result *d_results, const int32_t *d_pairs, const int64_t *pair_off,
+                   abea_read_summary *d_out, void *cuda_stream);
+
+/* Tab-separated text of eventalign rows (host arrays), one line per row:
+ *   read event kmer ref_pos ref_kmer model_kmer level model_mean model_stdv z
+ * k-mers as bases (lexicographic ranks over ACGT, first base most
+ * significant; "NNN..." for ref_rank -1), level, model_mean and model_stdv
+ * with 2 decimals, z with 3 (printf "%.2f" / "%.3f").  With header, a first
+ * line of the column names.  Writes at most cap bytes to buf (NUL
+ * terminated when cap > 0) and the full length (without the NUL) to
+ * *needed; ABEA_ERR_CAPACITY if it did not fit.  No CUDA call. */
+int abea_eventalign_tsv(const abea_eventalign_row *rows, int64_t n_rows, int k, int header, char *buf,
+                        size_t cap, size_t *needed);
+/* Tab-separated text of read summaries (host array), one line per read:
+ *   read status n_events n_kmers n_pairs first_event last_event events_aligned stays skips score
+ *   score_per_event flags
+ * scores with 3 decimals; otherwise as abea_eventalign_tsv. */
+int abea_summary_tsv(const abea_read_summary *s, int32_t n, int header, char *buf, size_t cap, size_t *needed);
+
 /* Event detection: raw signal -> events (thesis Sec. "Methylation calling":
  * the raw signal is segmented at sudden level changes, each segment an event
  * with the mean, standard deviation and duration of its samples; the thesis
@@ -239,6 +290,37 @@ int abea_estimate_scalings(abea_ctx *ctx, int32_t n, const uint8_t *d_seq, const
  * at most 31 lanes) always run one read per warp.  Returns ABEA_ERR_ARG for
  * a NaN theta. */
 int abea_set_block_mode(abea_ctx *ctx, double theta);
+
+/* Launch-geometry autotuner (the paper has no counterpart; results do not
+ * depend on it).  The per-read choice couples three knobs: a read runs
+ * either in per-warp mode (4 reads per CTA, one warp each; L = ceil(W/C)
+ * threads per band; a trace record of 2C words per band) or in block mode
+ * (1 read per CTA; its 4 warps share each band, 4 x L' threads; a record of
+ * 4 x 2C' words).  abea_autotune times both modes on a caller's sample of
+ * reads (host arrays as for abea_align_packed) for each length bucket of
+ * bands per read: [0, 4096), [4096, 16384), [16384, 65536), [65536, inf)
+ * (bands = events + k-mers + 1), two runs per mode after a warm-up, keeping
+ * the faster of each (device time of the core kernels).  Block mode is then
+ * used from the shortest bucket upward where it keeps winning: later batch
+ * calls of ctx at band width W run reads with at least that many bands in
+ * block mode (at most one per CTA, longest first) and the others per warp,
+ * instead of abea_set_block_mode's rule; abea_set_block_mode clears the
+ * tuning.  Writes one abea_tune_choice per bucket the sample populates (at
+ * most cap) and their number to *n_out.  W's without block mode (see
+ * abea_set_block_mode) tune to per-warp mode without running it. */
+typedef struct {
+    int32_t W;
+    int32_t min_bands, max_bands;   /* bucket: min_bands <= bands < max_bands (max_bands -1: unbounded) */
+    int32_t sample_reads;           /* the sample's reads in the bucket */
+    int32_t reads_per_cta;          /* chosen: 4 (per-warp mode) or 1 (block mode) */
+    int32_t threads_per_band;       /* chosen: L, or 4 x L' in block mode */
+    int32_t record_words;           /* chosen traceback layout: trace words per band */
+    float gcups_per_warp;           /* measured on the bucket's sample reads */
+    float gcups_block;              /* measured (0: block mode not available) */
+} abea_tune_choice;
+int abea_autotune(abea_ctx *ctx, int W, int32_t n, const char *seq, const int64_t *seq_off, const float *events,
+                  const int64_t *ev_off, const abea_scalings *sc, abea_tune_choice *out, int32_t cap,
+                  int32_t *n_out);
 
 /* Serving loop (the paper has no counterpart: it aligns files batch by
  * batch).  Requests (one read each) are admitted one at a time and aligned

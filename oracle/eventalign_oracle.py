@@ -54,3 +54,43 @@ def rows(read: int, model_mean, model_stdv, k: int, seq, events, scalings, pairs
             rr = int(r[0]) if r is not None and len(r) else -1
         out[t] = (read, e, j, rp, rr, mr, level, mean, stdv, z)
     return out
+
+
+SUMMARY_DTYPE = np.dtype([("read", "<i4"), ("status", "<i4"), ("n_events", "<i4"), ("n_kmers", "<i4"),
+                          ("n_pairs", "<i4"), ("first_event", "<i4"), ("last_event", "<i4"),
+                          ("events_aligned", "<i4"), ("stays", "<i4"), ("skips", "<i4"), ("score", "<f4"),
+                          ("score_per_event", "<f4"), ("flags", "<i4")])
+QC_NOT_ALIGNED, QC_TRIMMED, QC_SKIPS, QC_LOW_SCORE = 1, 2, 4, 8
+
+
+def read_summary(read: int, n_events: int, n_kmers: int, status: int, score, pairs) -> np.ndarray:
+    """Summary of one read's alignment (reading of f5c's eventalign --summary, which the thesis only
+    names): a walk over its pairs counting stays (next event, same k-mer) and skips (same event, next
+    k-mer); trimmed events before the first and after the last pair; FP32 score per event; the quality
+    flags NOT_ALIGNED (no alignment), TRIMMED (more than half of the events trimmed), SKIPS (skips
+    above a fifth of the k-mers), LOW_SCORE (score per event below -10)."""
+    p = np.asarray(pairs).reshape(-1, 2) if status == 0 else np.zeros((0, 2), np.int32)
+    stays = skips = 0
+    for t in range(1, len(p)):
+        de, dk = int(p[t, 0] - p[t - 1, 0]), int(p[t, 1] - p[t - 1, 1])
+        if (de, dk) == (1, 0):
+            stays += 1
+        elif (de, dk) == (0, 1):
+            skips += 1
+    first = int(p[0, 0]) if len(p) else -1
+    last = int(p[-1, 0]) if len(p) else -1
+    score = F(score)
+    spe = F(score / F(n_events)) if n_events > 0 else F(0)
+    if status != 0:
+        flags = QC_NOT_ALIGNED
+    else:
+        flags = 0
+        if first + (n_events - 1 - last) > n_events / 2:
+            flags |= QC_TRIMMED
+        if skips > n_kmers / 5:
+            flags |= QC_SKIPS
+        if spe < F(-10):
+            flags |= QC_LOW_SCORE
+    out = np.zeros(1, SUMMARY_DTYPE)
+    out[0] = (read, status, n_events, n_kmers, len(p), first, last, len(p) - skips, stays, skips, score, spe, flags)
+    return out

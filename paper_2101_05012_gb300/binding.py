@@ -30,7 +30,8 @@ SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
            "abea_set_block_mode", "abea_eventalign", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
-           "abea_server_stop", "abea_align_batch_device_noalloc", "abea_f32_from_i64"]
+           "abea_server_stop", "abea_align_batch_device_noalloc", "abea_f32_from_i64", "abea_summarise",
+           "abea_eventalign_tsv", "abea_summary_tsv", "abea_autotune"]
 
 
 class Scalings(ctypes.Structure):
@@ -58,6 +59,16 @@ EVENTALIGN_DTYPE = np.dtype([("read", "<i4"), ("event", "<i4"), ("kmer", "<i4"),
                              ("model_stdv", "<f4"), ("z", "<f4")])
 
 EVENT_DTYPE = np.dtype([("mean", "<f4"), ("stdv", "<f4"), ("start", "<i4"), ("length", "<i4")])
+
+TUNE_DTYPE = np.dtype([("W", "<i4"), ("min_bands", "<i4"), ("max_bands", "<i4"), ("sample_reads", "<i4"),
+                       ("reads_per_cta", "<i4"), ("threads_per_band", "<i4"), ("record_words", "<i4"),
+                       ("gcups_per_warp", "<f4"), ("gcups_block", "<f4")])
+
+SUMMARY_DTYPE = np.dtype([("read", "<i4"), ("status", "<i4"), ("n_events", "<i4"), ("n_kmers", "<i4"),
+                          ("n_pairs", "<i4"), ("first_event", "<i4"), ("last_event", "<i4"),
+                          ("events_aligned", "<i4"), ("stays", "<i4"), ("skips", "<i4"), ("score", "<f4"),
+                          ("score_per_event", "<f4"), ("flags", "<i4")])
+QC_NOT_ALIGNED, QC_TRIMMED, QC_SKIPS, QC_LOW_SCORE = 1, 2, 4, 8
 
 RESULT_DTYPE = np.dtype([("score", "<f4"), ("status", "<i4"), ("n_pairs", "<i4"), ("e_end", "<i4"),
                          ("cells", "<i8")])
@@ -105,6 +116,11 @@ def load(path: Optional[str] = None):
     lib.abea_server_poll.argtypes = [P, i64, i32, ctypes.POINTER(Result), P, i32, ctypes.POINTER(ctypes.c_double)]
     lib.abea_server_stop.argtypes = [P]
     lib.abea_align_batch_device_noalloc.argtypes = [ctypes.c_int, P, P, i32, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+    lib.abea_summarise.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.abea_autotune.argtypes = [P, ctypes.c_int, i32, P, P, P, P, P, P, i32, ctypes.POINTER(i32)]
+    lib.abea_eventalign_tsv.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    lib.abea_summary_tsv.argtypes = [P, i32, ctypes.c_int, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     for f in EXPORTS:
         if f not in ("abea_destroy", "abea_strerror"):
             getattr(lib, f).restype = ctypes.c_int
@@ -257,6 +273,26 @@ class Context:
             ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(d_status.data_ptr()), ctypes.c_void_p(stream)),
             "abea_estimate_scalings")
 
+    def summarise(self, n: int, seq_off, ev_off, d_results, d_pairs, pair_off, d_out, stream=None):
+        """abea_summarise: d_results and d_pairs as filled by align_batch_device, d_out a torch CUDA
+        tensor of n * 52 bytes; offsets are host numpy arrays."""
+        so = np.ascontiguousarray(seq_off, np.int64)
+        eo = np.ascontiguousarray(ev_off, np.int64)
+        po = np.ascontiguousarray(pair_off, np.int64)
+        _check(self.lib.abea_summarise(self.h, n, _p(so), _p(eo), ctypes.c_void_p(d_results.data_ptr()),
+                                       ctypes.c_void_p(d_pairs.data_ptr()), _p(po), ctypes.c_void_p(d_out.data_ptr()),
+                                       ctypes.c_void_p(stream)), "abea_summarise")
+
+    def autotune(self, batch, W: Optional[int] = None) -> np.ndarray:
+        """abea_autotune on a synth.Batch sample; returns the choices (TUNE_DTYPE)."""
+        W = batch.W if W is None else W
+        out = np.zeros(4, TUNE_DTYPE)
+        n_out = ctypes.c_int32()
+        sc = np.ascontiguousarray(batch.scalings, np.float32)
+        _check(self.lib.abea_autotune(self.h, W, batch.n, _p(batch.seq), _p(batch.seq_off), _p(batch.events),
+                                      _p(batch.ev_off), _p(sc), _p(out), 4, ctypes.byref(n_out)), "abea_autotune")
+        return out[:n_out.value].copy()
+
     def set_block_mode(self, theta: float):
         """Reads above theta x the even per-warp share of bands run on a whole block (<= 0: never)."""
         _check(self.lib.abea_set_block_mode(self.h, float(theta)), "abea_set_block_mode")
@@ -346,6 +382,28 @@ def f32_from_i64(d_in, d_out, stream=None):
     lib = load()
     _check(lib.abea_f32_from_i64(ctypes.c_void_p(d_in.data_ptr()), ctypes.c_int64(d_in.numel()),
                                  ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(stream)), "abea_f32_from_i64")
+
+
+def _text(fn, *args) -> str:
+    need = ctypes.c_size_t()
+    rc = fn(*args, None, 0, ctypes.byref(need))
+    if rc not in (ABEA_OK, ABEA_ERR_CAPACITY):
+        _check(rc, fn.__name__)
+    buf = ctypes.create_string_buffer(need.value + 1)
+    _check(fn(*args, buf, need.value + 1, ctypes.byref(need)), fn.__name__)
+    return buf.value.decode()
+
+
+def eventalign_tsv(rows: np.ndarray, k: int, header: bool = True) -> str:
+    """abea_eventalign_tsv over host rows (EVENTALIGN_DTYPE)."""
+    r = np.ascontiguousarray(rows, EVENTALIGN_DTYPE)
+    return _text(load().abea_eventalign_tsv, _p(r), ctypes.c_int64(len(r)), k, 1 if header else 0)
+
+
+def summary_tsv(summaries: np.ndarray, header: bool = True) -> str:
+    """abea_summary_tsv over host summaries (SUMMARY_DTYPE)."""
+    s = np.ascontiguousarray(summaries, SUMMARY_DTYPE)
+    return _text(load().abea_summary_tsv, _p(s), len(s), 1 if header else 0)
 
 
 def results_from_bytes(buf: np.ndarray) -> np.ndarray:

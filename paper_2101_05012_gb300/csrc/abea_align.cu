@@ -936,10 +936,11 @@ __device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float 
 template <int C, bool MIXED>
 __device__ __forceinline__ void wkill_dead(const ReadCtx &r, float (&S)[C])
 {
-    if (!MIXED) return;
+    if constexpr (MIXED) {
 #pragma unroll
-    for (int i = 0; i < C; i++)
-        if (r.dead_mask & (1u << i)) S[i] = neg_inf();
+        for (int i = 0; i < C; i++)
+            if (r.dead_mask & (1u << i)) S[i] = neg_inf();
+    }
 }
 
 // One band of a lean run (band b-1 and band b lie wholly in the matrix and

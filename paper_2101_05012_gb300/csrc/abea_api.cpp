@@ -62,6 +62,8 @@ struct abea_ctx {
     std::vector<float> h_mean, h_stdv;          // the model as set (host copy)
     int grid[9][2][2][3] = {};
     double block_theta = abea::kDefaultBlockTheta;   // block mode for reads above theta x the even share
+    int tune_W = 0;                             // band width abea_autotune tuned (0: none)
+    int64_t tune_block_min_bands = -1;          // tuned: reads with at least this many bands in block mode
     cudaMemPool_t pool = nullptr;               // the working buffers (stream-ordered: growing one never
                                                 // synchronises the device)
 };
@@ -247,7 +249,16 @@ int run_wave(abea_ctx *c, const Geometry &g, int32_t n, const Footprint &f, cons
     int &grid = c->grid[g.C][g.mixed ? 1 : 0][g.full ? 1 : 0][g.cg];
     if (grid <= 0) grid = abea::align_grid_size(g, c->device);
     if (grid <= 0) return ABEA_ERR_CUDA;
-    const int n_group = abea::group_count(h_rd, h_order, n, g, grid, c->block_theta);
+    int n_group;
+    if (c->tune_W == W) {                       // tuned: block mode for the reads of the tuned length buckets
+        n_group = 0;
+        if (g.cg > 0)
+            while (n_group < n && n_group < grid && !h_rd[h_order[n_group]].host_bad &&
+                   (int64_t)h_rd[h_order[n_group]].n_e + h_rd[h_order[n_group]].n_k + 1 >= c->tune_block_min_bands)
+                n_group++;
+    } else {
+        n_group = abea::group_count(h_rd, h_order, n, g, grid, c->block_theta);
+    }
     AlignArgs a;
     a.rd = (const ReadDesc *)c->rd.p;
     a.order = (const int32_t *)c->order.p;
@@ -353,6 +364,46 @@ size_t read_bytes(const abea_ctx *c, const Geometry &g, int64_t n_e, int64_t seq
     const Footprint f = footprint(std::max<int64_t>(n_e, 0), std::max<int64_t>(n_k, 0), g);
     return work_bytes(1, f) + (size_t)seq_len + 4 * (size_t)std::max<int64_t>(n_e, 0) + 8 * (size_t)pair_cap +
            sizeof(abea_result);
+}
+
+// Bounded text output of the TSV writers: writes what fits (always NUL
+// terminated when cap > 0) and counts the full length.
+struct TextOut {
+    char *buf;
+    size_t cap;
+    size_t len = 0;
+    void put(const char *s)
+    {
+        const size_t l = std::strlen(s);
+        if (len < cap) {
+            const size_t room = cap - len - 1;
+            std::memcpy(buf + len, s, std::min(room, l));
+        }
+        len += l;
+    }
+    template <class... A>
+    void printf(const char *fmt, A... a)
+    {
+        char line[512];
+        const int l = std::snprintf(line, sizeof(line), fmt, a...);
+        if (l > 0) put(line);
+    }
+    int finish(size_t *needed)
+    {
+        if (cap > 0) buf[std::min(len, cap - 1)] = '\0';
+        *needed = len;
+        return len < cap ? ABEA_OK : ABEA_ERR_CAPACITY;
+    }
+};
+
+// k-mer of lexicographic rank r over ACGT (first base most significant); "NNN.." for a negative rank.
+void kmer_text(int32_t r, int k, char *out)
+{
+    for (int t = k - 1; t >= 0; t--) {
+        out[t] = r < 0 ? 'N' : "ACGT"[r & 3];
+        if (r >= 0) r >>= 2;
+    }
+    out[k] = '\0';
 }
 
 }  // namespace
@@ -709,6 +760,74 @@ int abea_eventalign(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t 
     return cuda_err(cudaEventRecord(c->batch_done, st));
 }
 
+int abea_summarise(abea_ctx *c, int32_t n, const int64_t *seq_off, const int64_t *ev_off,
+                   const abea_result *d_results, const int32_t *d_pairs, const int64_t *pair_off,
+                   abea_read_summary *d_out, void *cuda_stream)
+{
+    if (!c) return ABEA_ERR_ARG;
+    if (c->k <= 0) return ABEA_ERR_NO_MODEL;
+    if (n < 0) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    if (!seq_off || !ev_off || !pair_off || !d_results || !d_out || (!d_pairs && pair_off[n] > pair_off[0]))
+        return ABEA_ERR_ARG;
+    for (int32_t i = 0; i < n; i++)
+        if (seq_off[i + 1] < seq_off[i] || ev_off[i + 1] < ev_off[i] || pair_off[i + 1] < pair_off[i])
+            return ABEA_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(cudaErrorInvalidDevice);
+    cudaStream_t st = pick_stream(c, cuda_stream);
+    int rc;
+    if ((rc = order_after_previous(c, st))) return rc;
+    const size_t m = (size_t)(n + 1);
+    const size_t bytes = 3 * m * sizeof(int64_t);
+    if ((rc = cuda_err(cudaEventSynchronize(c->upload_done)))) return rc;
+    if ((rc = ensure_host(c->h_ea_meta, bytes))) return rc;
+    int64_t *h = (int64_t *)c->h_ea_meta.p;
+    std::memcpy(h, seq_off, m * sizeof(int64_t));
+    std::memcpy(h + m, ev_off, m * sizeof(int64_t));
+    std::memcpy(h + 2 * m, pair_off, m * sizeof(int64_t));
+    if ((rc = ensure_dev(c, c->ea_meta, bytes, st))) return rc;
+    if ((rc = cuda_err(cudaMemcpyAsync(c->ea_meta.p, h, bytes, cudaMemcpyHostToDevice, st)))) return rc;
+    if ((rc = cuda_err(cudaEventRecord(c->upload_done, st)))) return rc;
+    if ((rc = cuda_err((cudaError_t)abea::launch_summary((const int64_t *)c->ea_meta.p, n, c->k, d_results, d_pairs,
+                                                          d_out, st))))
+        return rc;
+    c->last_launches++;
+    return cuda_err(cudaEventRecord(c->batch_done, st));
+}
+
+int abea_eventalign_tsv(const abea_eventalign_row *rows, int64_t n_rows, int k, int header, char *buf, size_t cap,
+                        size_t *needed)
+{
+    if (n_rows < 0 || k < 1 || k > 15 || (n_rows > 0 && !rows) || (cap > 0 && !buf) || !needed) return ABEA_ERR_ARG;
+    TextOut o{buf, cap};
+    if (header) o.put("read\tevent\tkmer\tref_pos\tref_kmer\tmodel_kmer\tlevel\tmodel_mean\tmodel_stdv\tz\n");
+    char rk[16], mk[16];
+    for (int64_t t = 0; t < n_rows; t++) {
+        const abea_eventalign_row &r = rows[t];
+        kmer_text(r.ref_rank, k, rk);
+        kmer_text(r.model_rank, k, mk);
+        o.printf("%d\t%d\t%d\t%d\t%s\t%s\t%.2f\t%.2f\t%.2f\t%.3f\n", r.read, r.event, r.kmer, r.ref_pos, rk, mk,
+                 (double)r.level, (double)r.model_mean, (double)r.model_stdv, (double)r.z);
+    }
+    return o.finish(needed);
+}
+
+int abea_summary_tsv(const abea_read_summary *s, int32_t n, int header, char *buf, size_t cap, size_t *needed)
+{
+    if (n < 0 || (n > 0 && !s) || (cap > 0 && !buf) || !needed) return ABEA_ERR_ARG;
+    TextOut o{buf, cap};
+    if (header)
+        o.put("read\tstatus\tn_events\tn_kmers\tn_pairs\tfirst_event\tlast_event\tevents_aligned\tstays\tskips"
+              "\tscore\tscore_per_event\tflags\n");
+    for (int32_t i = 0; i < n; i++) {
+        const abea_read_summary &r = s[i];
+        o.printf("%d\t%d\t%d\t%d\t%d\t%d\t%d\t%d\t%d\t%d\t%.3f\t%.3f\t%d\n", r.read, r.status, r.n_events,
+                 r.n_kmers, r.n_pairs, r.first_event, r.last_event, r.events_aligned, r.stays, r.skips,
+                 (double)r.score, (double)r.score_per_event, r.flags);
+    }
+    return o.finish(needed);
+}
+
 int abea_detect_events(abea_ctx *c, int32_t n, const int16_t *d_raw, const int64_t *raw_off,
                        const abea_calib *calib, int window, float tau2, abea_event *d_events,
                        const int64_t *event_off, int32_t *d_n_events, void *cuda_stream)
@@ -810,6 +929,102 @@ int abea_set_block_mode(abea_ctx *c, double theta)
 {
     if (!c || std::isnan(theta)) return ABEA_ERR_ARG;
     c->block_theta = theta;
+    c->tune_W = 0;
+    return ABEA_OK;
+}
+
+int abea_autotune(abea_ctx *c, int W, int32_t n, const char *seq, const int64_t *seq_off, const float *events,
+                  const int64_t *ev_off, const abea_scalings *sc, abea_tune_choice *out, int32_t cap, int32_t *n_out)
+{
+    int rc = check_common(c, W);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!seq || !seq_off || !events || !ev_off || !sc)) || cap < 0 || (cap > 0 && !out) || !n_out)
+        return ABEA_ERR_ARG;
+    *n_out = 0;
+    const Geometry g = abea::geometry_for(W);
+    const int64_t bounds[5] = {0, 4096, 16384, 65536, INT64_MAX};
+    const double saved_theta = c->block_theta;
+    c->tune_W = 0;                              // time the two modes, not the old choice
+    bool block_wins[4] = {false, false, false, false};
+    bool populated[4] = {false, false, false, false};
+    int32_t n_choices = 0;
+    for (int bk = 0; bk < 4; bk++) {
+        // the bucket's sample reads, packed
+        std::vector<char> s;
+        std::vector<float> e;
+        std::vector<int64_t> so(1, 0), eo(1, 0), po(1, 0);
+        std::vector<abea_scalings> sv;
+        for (int32_t i = 0; i < n; i++) {
+            const int64_t ne = ev_off[i + 1] - ev_off[i], nb = seq_off[i + 1] - seq_off[i];
+            const int64_t bands = ne + (nb - c->k + 1) + 1;
+            if (ne < 1 || nb < c->k || bands < bounds[bk] || bands >= bounds[bk + 1]) continue;
+            s.insert(s.end(), seq + seq_off[i], seq + seq_off[i + 1]);
+            e.insert(e.end(), events + ev_off[i], events + ev_off[i + 1]);
+            so.push_back((int64_t)s.size());
+            eo.push_back((int64_t)e.size());
+            po.push_back(po.back() + ne + (nb - c->k + 1));
+            sv.push_back(sc[i]);
+        }
+        const int32_t m = (int32_t)sv.size();
+        if (m == 0) continue;
+        populated[bk] = true;
+        std::vector<abea_result> res(m);
+        std::vector<int32_t> pairs((size_t)std::max<int64_t>(po.back(), 1) * 2);
+        float rate[2] = {0.0f, 0.0f};
+        for (int mode = 0; mode < 2; mode++) {
+            if (mode == 1 && g.cg == 0) break;
+            c->block_theta = mode == 0 ? 0.0 : 1e-300;   // 1e-300: every read above any share (one per CTA)
+            float best = 0.0f;
+            for (int rep = 0; rep < 3; rep++) {
+                abea_last_launch_stats(c, nullptr, nullptr);
+                if ((rc = abea_align_packed(c, m, W, s.data(), so.data(), e.data(), eo.data(), sv.data(), res.data(),
+                                            pairs.data(), po.data(), nullptr))) {
+                    c->block_theta = saved_theta;
+                    return rc;
+                }
+                float ms = 0.0f;
+                if ((rc = abea_last_launch_stats(c, nullptr, &ms))) {
+                    c->block_theta = saved_theta;
+                    return rc;
+                }
+                double cells = 0.0;
+                for (int32_t t = 0; t < m; t++) cells += (double)res[t].cells;
+                const float gcups = ms > 0.0f ? (float)(cells / ((double)ms * 1e6)) : 0.0f;
+                if (rep > 0) best = std::max(best, gcups);   // rep 0 warms up
+            }
+            rate[mode] = best;
+        }
+        block_wins[bk] = g.cg > 0 && rate[1] > rate[0];
+        if (n_choices < cap) {
+            abea_tune_choice &o = out[n_choices];
+            o.W = W;
+            o.min_bands = (int32_t)bounds[bk];
+            o.max_bands = bk == 3 ? -1 : (int32_t)bounds[bk + 1];
+            o.sample_reads = m;
+            o.reads_per_cta = block_wins[bk] ? 1 : 4;
+            o.threads_per_band = block_wins[bk] ? (W / 4 / std::max(g.cg, 1)) * 4 : g.L;
+            o.record_words = g.rec_words;
+            o.gcups_per_warp = rate[0];
+            o.gcups_block = rate[1];
+        }
+        n_choices++;
+    }
+    // block mode from the shortest populated bucket upward where it keeps winning
+    int64_t min_bands = INT64_MAX;
+    for (int bk = 3; bk >= 0; bk--) {
+        if (!populated[bk]) continue;
+        if (!block_wins[bk]) break;
+        min_bands = bounds[bk];
+    }
+    for (int32_t t = 0; t < std::min(n_choices, cap); t++) {   // report what later batches will do
+        const bool blk = out[t].min_bands >= min_bands;
+        out[t].reads_per_cta = blk ? 1 : 4;
+        out[t].threads_per_band = blk ? (W / 4 / std::max(g.cg, 1)) * 4 : g.L;
+    }
+    c->block_theta = saved_theta;
+    c->tune_W = W;
+    c->tune_block_min_bands = min_bands;
+    *n_out = std::min(n_choices, cap);
     return ABEA_OK;
 }
 

@@ -228,7 +228,76 @@ __global__ void __launch_bounds__(kThreads, 5) eventalign_kernel(const int64_t *
     }
 }
 
+// Read summaries: one warp per read (grid-stride); the lanes count stays and
+// skips over consecutive pairs, lane 0 writes the record.
+__global__ void __launch_bounds__(kThreads) summary_kernel(const int64_t *__restrict__ meta, int32_t n, int k,
+                                                           const abea_result *__restrict__ res,
+                                                           const int32_t *__restrict__ pairs,
+                                                           abea_read_summary *__restrict__ out)
+{
+    const int64_t *seq_off = meta, *ev_off = meta + (n + 1), *pair_off = meta + 2 * (n + 1);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const abea_result r = res[i];
+        const int32_t n_e = (int32_t)(ev_off[i + 1] - ev_off[i]);
+        const int32_t n_k = (int32_t)(seq_off[i + 1] - seq_off[i]) - k + 1;
+        const bool ok = r.status == ABEA_READ_OK;
+        const int32_t np = ok ? r.n_pairs : 0;
+        const int2 *p = reinterpret_cast<const int2 *>(pairs) + pair_off[i];
+        int stays = 0, skips = 0;
+        for (int32_t t = 1 + lane; t < np; t += 32) {
+            const int2 a = p[t - 1], b = p[t];
+            stays += (b.x == a.x + 1 && b.y == a.y) ? 1 : 0;
+            skips += (b.x == a.x && b.y == a.y + 1) ? 1 : 0;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            stays += __shfl_xor_sync(0xffffffffu, stays, off);
+            skips += __shfl_xor_sync(0xffffffffu, skips, off);
+        }
+        if (lane == 0) {
+            abea_read_summary s;
+            s.read = i;
+            s.status = r.status;
+            s.n_events = n_e;
+            s.n_kmers = n_k;
+            s.n_pairs = np;
+            s.first_event = np > 0 ? p[0].x : -1;
+            s.last_event = np > 0 ? p[np - 1].x : -1;
+            s.stays = stays;
+            s.skips = skips;
+            s.events_aligned = np - skips;
+            s.score = r.score;
+            s.score_per_event = n_e > 0 ? __fdiv_rn(r.score, (float)n_e) : 0.0f;
+            int flags = 0;
+            if (!ok) {
+                flags = ABEA_QC_NOT_ALIGNED;
+            } else {
+                if (2 * (s.first_event + (n_e - 1 - s.last_event)) > n_e) flags |= ABEA_QC_TRIMMED;
+                if (5 * skips > n_k) flags |= ABEA_QC_SKIPS;
+                if (s.score_per_event < -10.0f) flags |= ABEA_QC_LOW_SCORE;
+            }
+            s.flags = flags;
+            out[i] = s;
+        }
+    }
+}
+
 }  // namespace
+
+int launch_summary(const int64_t *meta, int32_t n, int k, const abea_result *res, const int32_t *pairs,
+                   abea_read_summary *out, void *stream)
+{
+    if (n <= 0) return (int)cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    const int64_t blocks = ((int64_t)n + kThreads / 32 - 1) / (kThreads / 32);
+    summary_kernel<<<(unsigned)std::min<int64_t>(blocks, (int64_t)sms * 8), kThreads, 0, (cudaStream_t)stream>>>(
+        meta, n, k, res, pairs, out);
+    return (int)cudaGetLastError();
+}
 
 int launch_eventalign(const int64_t *meta, int32_t n, int64_t total_slots, const uint8_t *seq, int64_t seq_lo,
                       int64_t seq_hi, int2 *ranks, const float *events, const abea_scalings *sc, const abea_result *res, const int32_t *pairs,

@@ -76,6 +76,9 @@ int launch_eventalign(const int64_t *meta, int32_t n, int64_t total_slots, const
                       int64_t seq_hi, int2 *ranks, const float *events, const abea_scalings *sc, const abea_result *res, const int32_t *pairs,
                       const int32_t *ref_pos, const uint8_t *ref, int64_t ref_len, const float2 *model_f, int k,
                       int scale_events, abea_eventalign_row *rows, void *stream);
+// Read summaries (meta as for eventalign: seq_off, ev_off, pair_off, n+1 each).
+int launch_summary(const int64_t *meta, int32_t n, int k, const abea_result *res, const int32_t *pairs,
+                   abea_read_summary *out, void *stream);
 // Event detection runs over tiles of kEventTile positions (a read of len
 // samples has ceil(len / kEventTile) tiles; tile_off is their prefix over the
 // reads, tile_read the read of each tile).  scratch holds event_tile_bytes()

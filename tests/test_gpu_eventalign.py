@@ -18,6 +18,8 @@ def test_rows_match_the_oracle():
     evs, sqs, scs = zip(*[b0.read(i) for i in range(b0.n)])
     sqs = list(sqs)
     sqs[5] = sqs[5][:100] + b"N" + sqs[5][101:]
+    evs = list(evs)
+    evs[7] = np.full_like(evs[7], 400.0)        # every event far off the model: trimmed, low score
     b = synth.custom_batch(list(evs), sqs, list(scs), b0.model_mean, b0.model_stdv, b0.k, b0.W)
     # one reference holding every read's reference, with per-base positions into it
     refs, pos = [], np.zeros(len(b.seq), np.int32)
@@ -48,9 +50,22 @@ def test_rows_match_the_oracle():
                            len(ref), mode, d_rows, stream=s.cuda_stream)
             s.synchronize()
             out[mode] = np.frombuffer(d_rows.cpu().numpy().tobytes(), binding.EVENTALIGN_DTYPE)
+        d_sum = torch.zeros(b.n * binding.SUMMARY_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ctx.summarise(b.n, b.seq_off, b.ev_off, d_res, d_pairs, po, d_sum, stream=s.cuda_stream)
+        s.synchronize()
+        summ = np.frombuffer(d_sum.cpu().numpy().tobytes(), binding.SUMMARY_DTYPE)
         res = binding.results_from_bytes(d_res.cpu().numpy())
         pairs = d_pairs.cpu().numpy().reshape(-1, 2)
     assert res["status"][5] == binding.READ_BAD_INPUT and np.sum(res["status"] == 0) == b.n - 1
+    # per-read summaries against the oracle's, from the same alignments
+    for i in range(b.n):
+        want = ea.read_summary(i, int(b.n_events()[i]), int(b.n_kmers()[i]), int(res["status"][i]),
+                               res["score"][i], pairs[po[i]:po[i] + res["n_pairs"][i]])
+        for f in binding.SUMMARY_DTYPE.names:
+            assert np.array_equal(summ[f][i], want[f][0]), (i, f, summ[f][i], want[f][0])
+    assert summ["flags"][5] == binding.QC_NOT_ALIGNED
+    assert summ["flags"][7] & (binding.QC_TRIMMED | binding.QC_LOW_SCORE)
+    assert np.all(summ["flags"][[i for i in range(b.n) if i not in (5, 7)]] == 0)
     for mode in (False, True):
         rows = out[mode]
         for i in range(b.n):
