@@ -674,18 +674,18 @@ __device__ __forceinline__ unsigned chunk_event_moves(const ReadCtx &r, int top,
 // (t < cap).  Returns 0, or -1 if a traced cell lies outside its band (cannot
 // happen); n_out = pairs walked.  The records of 96 bands sit in a
 // shared-memory ring of three 32-band chunks, the next two always on their
-// way (cp.async).  Within a chunk a step is one shared-memory load and a
-// few bit operations: the band moves of this chunk and the next sit in two
-// words (one funnel shift gives the two that a step needs), and the step's
-// two index decrements are appended to two bit masks.  At the end of each
-// chunk the warp writes the chunk's pairs at once, lane t the t-th, its
-// indices from the masks' prefix counts.
+// way (cp.async).  Within a chunk a step is one shared-memory load, a few
+// bit operations and one shared-memory store of the step's cell into the
+// stage (32 pairs, the same value from every lane): the band moves of this
+// chunk and the next sit in two words (one funnel shift gives the two that a
+// step needs).  At the end of each chunk the warp writes the chunk's pairs
+// from the stage at once, lane t the t-th.
 // Record layout: per-warp mode, offset j is bit j/C of word pair j%C of a
 // record of R words; block mode (GROUP), offset j = gw*W' + C*lane + i is
 // bit lane of word pair gw*C + i, W' = wg (wg_magic = ceil(2^32 / wg)).
 template <int C, int R, bool FULLW, bool GROUP>
-__device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end, int2 *out, int cap, int &n_out,
-                         unsigned wg = 1, unsigned wg_magic = 0)
+__device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int2 *stage, int e_end, int le_end, int2 *out, int cap,
+                         int &n_out, unsigned wg = 1, unsigned wg_magic = 0)
 {
     constexpr int RING = 3 * kChunk;
     int e = e_end, k = r.n_k - 1;
@@ -705,9 +705,7 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
     bool bad = false;
     for (;;) {
         const uint32_t *rec = bufs + base * R;
-        const int e0 = e, k0 = k;
-        unsigned de_bits = 0, dk_bits = 0;
-        int nb = 0;
+        int2 *sp = stage;
         // One step of the walk.  A cell outside its band (it cannot happen) is noted at the end of
         // the chunk from the largest offset seen; the load index stays inside the record either way.
         unsigned jmax = 0;
@@ -730,12 +728,10 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
             const unsigned d = (((w.x >> bit) | l) & 1u) ^ 1u;      // D: neither L nor U
             const unsigned ev = __funnelshift_r(em_lo, em_hi, off);  // bit 0: band top-off, bit 1: the one below
             le -= (int)((ev & 1u) + ((ev >> 1) & d));
+            *sp++ = make_int2(e, k);
             const unsigned de = l ^ 1u, dk = l | d;                 // U or D: e-1; L or D: k-1
             e -= (int)de;
             k -= (int)dk;
-            de_bits |= de << nb;
-            dk_bits |= dk << nb;
-            nb++;
             off += 1 + (int)d;
         };
         while (off <= kChunk - 4 && e >= 1 && k >= 1) {      // two steps stay in the chunk and the matrix
@@ -744,10 +740,11 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int e_end, int le_end
         }
         while (off < kChunk && (e | k) >= 0) step();         // at most 32 steps in all per chunk
         bad |= jmax >= (unsigned)r.W;
+        const int nb = (int)(sp - stage);
+        __syncwarp();
         if (r.lane < nb) {             // the chunk's pairs, one per lane
-            const unsigned below = (1u << r.lane) - 1u;
             const int t = n + r.lane;
-            if (t < cap) out[cap - 1 - t] = make_int2(e0 - __popc(de_bits & below), k0 - __popc(dk_bits & below));
+            if (t < cap) out[cap - 1 - t] = stage[r.lane];
         }
         n += nb;
         if ((e | k) < 0 || bad) break;
@@ -801,7 +798,9 @@ __device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lan
 // The event and k-mer operands entering the band come from two rings in
 // shared memory per warp (128 events, 128 k-mer cache entries), filled 32
 // at a time by cp.async at the start of each run of bands, so that each
-// band takes its entering operand with one shared-memory load.
+// band takes its entering operand with one shared-memory load.  K-mer k
+// sits in slot (k - W') mod 128 and event e in slot (e - 1) mod 128: the
+// operands entering on the next move are then at slots ll_k and ll_e.
 
 constexpr int kRing = 128;        // entries per operand ring
 constexpr int kRingAhead = 96;    // entries requested past the next entering one at each run start
@@ -837,14 +836,14 @@ __device__ __forceinline__ void wring_refill(WLane<C> &s, const ReadCtx &r)
     const int k_next = s.ll_k + r.Wp, e_next = s.ll_e + 1;
     while (s.k_req < k_next + kRingAhead) {
         const int k = s.k_req + r.lane;
-        float4 *dst = s.ring->k + (k & (kRing - 1));
+        float4 *dst = s.ring->k + ((k - r.Wp) & (kRing - 1));
         if ((unsigned)k < (unsigned)r.n_k) cp_async16(dst, r.kc + k);
         else *dst = no_kmer();
         s.k_req += 32;
     }
     while (s.e_req < e_next + kRingAhead) {
         const int e = s.e_req + r.lane;
-        float *dst = s.ring->e + (e & (kRing - 1));
+        float *dst = s.ring->e + ((e - 1) & (kRing - 1));
         if ((unsigned)e < (unsigned)r.n_e) {
             const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(r.ev + e) : "memory");
@@ -863,16 +862,17 @@ __device__ __forceinline__ void wring_wait()
     __syncwarp();
 }
 
-// The operands entering on the next k-mer move (k-mer ll_k + W') and event move (event ll_e + 1).
+// The operands entering on the next k-mer move (k-mer ll_k + W', ring slot ll_k) and event move
+// (event ll_e + 1, ring slot ll_e).
 template <int C>
-__device__ __forceinline__ void wnext_kmer(WLane<C> &s, const ReadCtx &r)
+__device__ __forceinline__ void wnext_kmer(WLane<C> &s, const ReadCtx &)
 {
-    s.kin = s.ring->k[(s.ll_k + r.Wp) & (kRing - 1)];
+    s.kin = s.ring->k[s.ll_k & (kRing - 1)];
 }
 template <int C>
 __device__ __forceinline__ void wnext_event(WLane<C> &s)
 {
-    s.xin = s.ring->e[(s.ll_e + 1) & (kRing - 1)];
+    s.xin = s.ring->e[s.ll_e & (kRing - 1)];
 }
 
 // Band b from S_{b-1} (P) and S_{b-2} (PP); S_b is written into PP and its
@@ -923,10 +923,12 @@ __device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float 
         const float diag = kp ? d_kp : d_ep;
         bool p0, p1;
         S[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
-        if (!FULLW && i == 0) p0 = r.lane31 ? KM : p0;     // the band's move, bit 31 of word 0
         w[2 * i] = __ballot_sync(kFull, p0);
         w[2 * i + 1] = __ballot_sync(kFull, p1);
     }
+    // the band's move in bit 31 of word 0: lane 31 lies above the band unless all 32 lanes are
+    // live, so its bits are 0 (its cells are -inf)
+    if (!FULLW && KM) w[0] |= 0x80000000u;
 #pragma unroll
     for (int i = 0; i < C; i++) PP[i] = S[i];
     s.qprev = qb;
@@ -964,21 +966,24 @@ __device__ __forceinline__ void wlean_band(WLane<C> &s, const ReadCtx &r, float 
     s.b = b + 1;
 }
 
-// m lean bands (m >= 1), two per iteration.  On exit P holds the last band
-// and PP the one before.
+// m lean bands (m >= 1), two per iteration and one test of the count per
+// iteration; an odd count enters at the second band with the two arrays
+// swapped.  On exit P holds the last band and PP the one before.
 template <int C, bool MIXED, bool FULLW>
 __device__ __forceinline__ void wlean_run(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C], int m)
 {
+    int t = (m + 1) >> 1;             // second bands to run
+    if (m & 1) {
+        swap_bands(P, PP);
+        goto second;
+    }
     for (;;) {
         if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, P, PP);
         else wlean_band<C, MIXED, FULLW, false>(s, r, P, PP);
-        if (--m == 0) {
-            swap_bands(P, PP);
-            return;
-        }
+    second:
         if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, PP, P);
         else wlean_band<C, MIXED, FULLW, false>(s, r, PP, P);
-        if (--m == 0) return;
+        if (--t == 0) return;
     }
 }
 
@@ -1187,7 +1192,8 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
         status = ABEA_READ_FAIL_NO_END;
     } else {
         __syncwarp();                         // lane 0's trace stores are visible to the warp
-        const int rc = backtrack<C, Rec<C>::R, FULLW, false>(r, bt_bufs, best_e, best_le, out, cap, n);
+        const int rc = backtrack<C, Rec<C>::R, FULLW, false>(r, bt_bufs, reinterpret_cast<int2 *>(rings->k), best_e,
+                                                             best_le, out, cap, n);
         if (rc != 0) {
             status = ABEA_READ_FAIL_NO_END;   // internal inconsistency, reported as no alignment
             n = 0;
@@ -1210,6 +1216,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 
 // Shared state of block mode.
 struct GroupShared {
+    int2 stage[kChunk];                  // the walk's pairs of one chunk
     float2 xch[2][kWarps];
     float rx[kWarps];
     double best[kWarps];
@@ -1349,7 +1356,8 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
         status = ABEA_READ_FAIL_NO_END;
     } else {
         const unsigned magic = 0xffffffffu / (unsigned)Wg + 1u;
-        const int rc = backtrack<C, RG, false, true>(r, bt_bufs, best_e, best_le, out, cap, n, (unsigned)Wg, magic);
+        const int rc = backtrack<C, RG, false, true>(r, bt_bufs, gs.stage, best_e, best_le, out, cap, n, (unsigned)Wg,
+                                                     magic);
         if (rc != 0) {
             status = ABEA_READ_FAIL_NO_END;
             n = 0;
