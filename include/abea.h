@@ -387,18 +387,26 @@ int abea_server_stop(abea_server *srv);
  * No context is needed: the pore model (k <= 7, 4^k host floats each) is
  * passed with every call, and all working memory (model rows, per-read
  * descriptors, k-mer cache, trace) comes from one 64 MiB device array
- * compiled into the library, which every GPU that loads the library holds
- * until the process exits.  Inputs, outputs, offsets and scalings are as in
+ * compiled into the library.  A device holds the array from the moment the
+ * library's device code is loaded there until the process exits; under
+ * CUDA's lazy module loading (the default) that is the first call of this
+ * function on the device, so make that first call before the host
+ * application fills the device's memory (or set CUDA_MODULE_LOADING=EAGER);
+ * if the device has no room for the array then, the call returns
+ * ABEA_ERR_NOMEM.  Inputs, outputs, offsets and scalings are as in
  * abea_align_batch_device; the work runs on the current device, on
- * cuda_stream, and the call returns without waiting for it.
+ * cuda_stream.  The model rows and descriptors are copied from pageable
+ * host buffers, which CUDA may stage by first synchronising with the stream:
+ * the call can wait for earlier work on its own stream, never for other
+ * streams, and returns without waiting for its own kernels.
  * Returns ABEA_ERR_NOMEM, before issuing any work, when n > 16384 or the
  * batch's working set exceeds the 64 MiB array (at W = 100 about 0.33 B per
  * band cell plus 16 B per k-mer and 120 B per read).
  * Every call reuses the same array: calls whose work overlaps on the GPU
- * (different streams or host threads) race and must not be made; issue them
- * one after another on one stream, from one host thread at a time.  The first
- * call on a device looks up the array's device address, so make it before
- * any stream capture. */
+ * (different streams) race and must not be made; issue them one after
+ * another on one stream.  A lock serialises calls from several host threads.
+ * The first call on a device looks up the array's device address, so make it
+ * before any stream capture. */
 int abea_align_batch_device_noalloc(int k, const float *level_mean, const float *level_stdv,
                                     int32_t n, int W,
                                     const uint8_t *d_seq, const int64_t *seq_off,

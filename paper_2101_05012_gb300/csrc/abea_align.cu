@@ -265,8 +265,8 @@ __device__ __forceinline__ void group_exchange(Lane<C> &s, const ReadCtx &r, int
 }
 
 // The value of a band at offset W-1.
-template <int C, bool MIXED>
-__device__ __forceinline__ float far_end(const ReadCtx &r, const float (&S)[C])
+template <int C, bool MIXED, int N>
+__device__ __forceinline__ float far_end(const ReadCtx &r, const float (&S)[N])
 {
     if (!MIXED) return __shfl_sync(kFull, S[C - 1], r.L - 1);
     const int j = r.W - 1, slot = j % C;
@@ -788,12 +788,18 @@ __device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lan
 // ---------------------------------------------------------------------------
 // Per-warp mode.
 //
-// The band loop is unrolled by two (the two score arrays alternate roles),
-// with one branch per band on its move; the previous band's move selects
-// the diagonal operands at run time.  A compact loop keeps the code of the
-// hot path small enough for the instruction caches (state machines over
-// more than a handful of band variants ran slower, fetch-bound, although
-// they executed fewer instructions).
+// Scores: P[0..C-1] holds S_{b-1} at the lane's offsets; H holds band b-1's
+// view of S_{b-2} (the C+1 values that band b-1 took its left and up
+// neighbours from: Q[t] = S_{b-2}[C*lane + t - 1 + KM_{b-1}], t = 0..C),
+// stored rotated, H[m] = Q[(m + 1) mod (C+1)].  Band b's diagonal neighbour
+// of slot i is Q[i + KM_b], so it is read at an index fixed by band b's own
+// move; S_b is written over H, and P becomes the next band's H: in place
+// after an event move (H = {P[0..C-1], boundary}), rotated by one register
+// after a k-mer move.  The band loop is unrolled by two (the two arrays
+// alternate roles), with one branch per band on its move.  A compact loop
+// keeps the code of the hot path small enough for the instruction caches
+// (state machines over more than a handful of band variants ran slower,
+// fetch-bound, although they executed fewer instructions).
 //
 // The event and k-mer operands entering the band come from two rings in
 // shared memory per warp (128 events, 128 k-mer cache entries), filled 32
@@ -814,8 +820,6 @@ struct WRings {
 template <int C>
 struct WLane {
     float X[C], A[C], B[C], Cc[C];   // operands of the lane's offsets
-    float qprev;                     // boundary value of the previous band's shifted view
-    bool kprev;                      // the last band moved by one k-mer
     bool knext;                      // the next band moves by one k-mer (decided)
     int ll_e, ll_k;                  // offset-0 cell of the last computed band
     int b;                           // next band to compute
@@ -875,11 +879,12 @@ __device__ __forceinline__ void wnext_event(WLane<C> &s)
     s.xin = s.ring->e[s.ll_e & (kRing - 1)];
 }
 
-// Band b from S_{b-1} (P) and S_{b-2} (PP); S_b is written into PP and its
-// trace words into w.  KM: this band moves by one k-mer; s.kprev: the
-// previous band did.  FULLW: all 32 lanes are live (no lane above the band).
+// Band b from S_{b-1} (P[0..C-1]) and band b-1's view of S_{b-2} (H);
+// S_b is written into H[0..C-1] and its trace words into w, and P becomes
+// band b's view of S_{b-1} (the next band's H).  KM: this band moves by one
+// k-mer.  FULLW: all 32 lanes are live (no lane above the band).
 template <int C, bool KM, bool FULLW>
-__device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C],
+__device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1],
                                            uint32_t (&w)[2 * C])
 {
     if (KM) {
@@ -901,7 +906,8 @@ __device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float 
         for (int i = C - 1; i > 0; i--) s.X[i] = s.X[i - 1];
         s.X[0] = r.first_lane ? s.xin : sx;
     }
-    // Q[t] = S_{b-1}[C*lane + t - 1 + KM], t = 0..C: left of slot i is Q[i], up is Q[i+1].
+    // Q[t] = S_{b-1}[C*lane + t - 1 + KM], t = 0..C: left of slot i is Q[i], up is Q[i+1]; the
+    // one value from a neighbour lane is qb (Q[C] after a k-mer move, Q[0] after an event move).
     float qb;
     if (KM) {
         qb = __shfl_down_sync(kFull, P[0], 1);
@@ -910,33 +916,35 @@ __device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float 
         qb = __shfl_sync(kFull, P[C - 1], r.src_up);
         if (FULLW && r.first_lane) qb = neg_inf();
     }
-    const bool kp = s.kprev;
-    float S[C];
+    // the slots in descending order: slot i writes H[i] after slot i+1 has read it (event move)
 #pragma unroll
-    for (int i = 0; i < C; i++) {
+    for (int i = C - 1; i >= 0; i--) {
         const float left = KM ? P[i] : (i == 0 ? qb : P[i > 0 ? i - 1 : 0]);
         const float up = KM ? (i == C - 1 ? qb : P[i < C - 1 ? i + 1 : 0]) : P[i];
-        // diag = the previous band's Q at t = i + KM
-        const int t = i + (KM ? 1 : 0);
-        const float d_kp = (t == C) ? s.qprev : PP[t < C ? t : 0];
-        const float d_ep = (t == 0) ? s.qprev : PP[t > 0 ? t - 1 : 0];
-        const float diag = kp ? d_kp : d_ep;
+        // diag = band b-1's Q at t = i + KM, stored at H[(t + C) mod (C+1)]
+        const float diag = KM ? H[i] : H[i == 0 ? C : i - 1];
         bool p0, p1;
-        S[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
+        H[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
         w[2 * i] = __ballot_sync(kFull, p0);
         w[2 * i + 1] = __ballot_sync(kFull, p1);
     }
     // the band's move in bit 31 of word 0: lane 31 lies above the band unless all 32 lanes are
     // live, so its bits are 0 (its cells are -inf)
     if (!FULLW && KM) w[0] |= 0x80000000u;
+    // P becomes this band's Q, rotated: P[m] = Q[(m + 1) mod (C+1)]
+    if (KM) {                           // Q = {P[0..C-1], qb}
+        const float q0 = P[0];
 #pragma unroll
-    for (int i = 0; i < C; i++) PP[i] = S[i];
-    s.qprev = qb;
-    s.kprev = KM;
+        for (int m = 0; m < C - 1; m++) P[m] = P[m + 1];
+        P[C - 1] = qb;
+        P[C] = q0;
+    } else {                            // Q = {qb, P[0..C-1]}: P[0..C-1] stay
+        P[C] = qb;
+    }
 }
 
 template <int C, bool MIXED>
-__device__ __forceinline__ void wkill_dead(const ReadCtx &r, float (&S)[C])
+__device__ __forceinline__ void wkill_dead(const ReadCtx &r, float (&S)[C + 1])
 {
     if constexpr (MIXED) {
 #pragma unroll
@@ -946,19 +954,21 @@ __device__ __forceinline__ void wkill_dead(const ReadCtx &r, float (&S)[C])
 }
 
 // One band of a lean run (band b-1 and band b lie wholly in the matrix and
-// miss the end column).
+// miss the end column).  S_b ends in H, band b's view of S_{b-1} in P.  The
+// move of band b+1 compares two values every lane received from the same
+// lanes, so every lane takes the same decision without a vote.
 template <int C, bool MIXED, bool FULLW, bool KM>
-__device__ __forceinline__ void wlean_band(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+__device__ __forceinline__ void wlean_band(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1])
 {
     const int b = s.b;
     uint32_t w[2 * C];
-    wband_fill<C, KM, FULLW>(s, r, P, PP, w);
-    wkill_dead<C, MIXED>(r, PP);
+    wband_fill<C, KM, FULLW>(s, r, P, H, w);
+    wkill_dead<C, MIXED>(r, H);
     if (KM) s.ll_k++;
     else s.ll_e++;
-    const float lo = __shfl_sync(kFull, PP[0], 0);
-    const float hi = far_end<C, MIXED>(r, PP);
-    s.knext = __all_sync(kFull, lo < hi);
+    const float lo = __shfl_sync(kFull, H[0], 0);
+    const float hi = far_end<C, MIXED>(r, H);
+    s.knext = lo < hi;
     store_record<C>(r, b, w);
     if (FULLW && r.lane == 0) r.mv[b] = KM ? 1 : 0;
     if (KM) wnext_kmer(s, r);
@@ -970,35 +980,36 @@ __device__ __forceinline__ void wlean_band(WLane<C> &s, const ReadCtx &r, float 
 // iteration; an odd count enters at the second band with the two arrays
 // swapped.  On exit P holds the last band and PP the one before.
 template <int C, bool MIXED, bool FULLW>
-__device__ __forceinline__ void wlean_run(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C], int m)
+__device__ __forceinline__ void wlean_run(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1], int m)
 {
     int t = (m + 1) >> 1;             // second bands to run
     if (m & 1) {
-        swap_bands(P, PP);
+        swap_bands(P, H);
         goto second;
     }
     for (;;) {
-        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, P, PP);
-        else wlean_band<C, MIXED, FULLW, false>(s, r, P, PP);
+        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, P, H);
+        else wlean_band<C, MIXED, FULLW, false>(s, r, P, H);
     second:
-        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, PP, P);
-        else wlean_band<C, MIXED, FULLW, false>(s, r, PP, P);
+        if (s.knext) wlean_band<C, MIXED, FULLW, true>(s, r, H, P);
+        else wlean_band<C, MIXED, FULLW, false>(s, r, H, P);
         if (--t == 0) return;
     }
 }
 
-// One band b = s.b with every check (trim cell, end cell, cell count, bounds of the move).
+// One band b = s.b with every check (trim cell, end cell, cell count, bounds
+// of the move).  As wlean_band: S_b ends in H, band b's view of S_{b-1} in P.
 template <int C, bool MIXED, bool FULLW>
-__device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+__device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1])
 {
     const int b = s.b;
     const bool K = s.knext;
     uint32_t w[2 * C];
-    if (K) wband_fill<C, true, FULLW>(s, r, P, PP, w);
-    else wband_fill<C, false, FULLW>(s, r, P, PP, w);
+    if (K) wband_fill<C, true, FULLW>(s, r, P, H, w);
+    else wband_fill<C, false, FULLW>(s, r, P, H, w);
     if (K) s.ll_k++;
     else s.ll_e++;
-    wkill_dead<C, MIXED>(r, PP);
+    wkill_dead<C, MIXED>(r, H);
     // trim state: the cell (e,-1) scores (e+1)*lp_trim
     if (s.ll_k < 0) {
         const int jt = -1 - s.ll_k;
@@ -1006,7 +1017,7 @@ __device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float 
         const float v = (e >= 0 && e < r.n_e) ? __fmul_rn((float)(e + 1), r.cs.lp_trim) : neg_inf();
 #pragma unroll
         for (int i = 0; i < C; i++)
-            if (C * r.lane + i == jt) PP[i] = v;
+            if (C * r.lane + i == jt) H[i] = v;
     }
     // end cell candidates: (e, n_k-1) plus the n_e-1-e trailing events trimmed
     const int jend = r.n_k - 1 - s.ll_k;
@@ -1016,7 +1027,7 @@ __device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float 
 #pragma unroll
             for (int i = 0; i < C; i++) {
                 if (C * r.lane + i == jend) {
-                    const float rel = __fadd_rn(PP[i], __fmul_rn((float)(r.n_e - 1 - e), r.cs.lp_trim));
+                    const float rel = __fadd_rn(H[i], __fmul_rn((float)(r.n_e - 1 - e), r.cs.lp_trim));
                     const double cand = s.cold->frame + (double)rel;
                     if (cand > s.cold->best) {
                         s.cold->best = cand;
@@ -1032,8 +1043,8 @@ __device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float 
     s.cold->cells += max(0, jhi - jlo);
     // the move of band b+1: cells beyond the last k-mer count as -inf; both ends -inf: a k-mer
     // move on odd bands
-    float lo = __shfl_sync(kFull, PP[0], 0);
-    float hi = far_end<C, MIXED>(r, PP);
+    float lo = __shfl_sync(kFull, H[0], 0);
+    float hi = far_end<C, MIXED>(r, H);
     if (s.ll_k >= r.n_k) lo = neg_inf();
     if (s.ll_k + r.W - 1 >= r.n_k) hi = neg_inf();
     const bool kn = (lo == neg_inf() && hi == neg_inf()) ? (((b + 1) & 1) != 0) : (lo < hi);
@@ -1046,32 +1057,30 @@ __device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float 
 }
 
 // Exact renormalisation after a lean band with b % 64 == 0 (see
-// renormalise): P = S_b and PP = S_{b-1}, both wholly in the matrix.
+// renormalise): P[0..C-1] = S_b and H = band b's view of S_{b-1}, both bands
+// wholly in the matrix.  The view holds S_{b-1} at the lane's offsets and
+// one value of a neighbour lane's, so its maximum over the warp is S_{b-1}'s;
+// lanes above the band and masked slots hold -inf.
 template <int C>
-__device__ __forceinline__ void wrenormalise(WLane<C> &s, const ReadCtx &r, float (&Sb)[C], float (&Sb1)[C])
+__device__ __forceinline__ void wrenormalise(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1])
 {
-    float m = neg_inf();
-    if (r.lane < r.L) {
+    float m = H[C];
 #pragma unroll
-        for (int i = 0; i < C; i++)
-            if (!((r.dead_mask >> i) & 1u)) m = fmaxf(m, fmaxf(Sb[i], Sb1[i]));
-    }
+    for (int i = 0; i < C; i++) m = fmaxf(m, fmaxf(P[i], H[i]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
     if (m <= -2048.0f) {
         const float R = -1024.0f * floorf(__fmul_rn(-m, 1.0f / 1024.0f));
 #pragma unroll
-        for (int i = 0; i < C; i++) {
-            Sb[i] = __fsub_rn(Sb[i], R);
-            Sb1[i] = __fsub_rn(Sb1[i], R);
-        }
-        s.qprev = __fsub_rn(s.qprev, R);
+        for (int i = 0; i < C; i++) P[i] = __fsub_rn(P[i], R);
+#pragma unroll
+        for (int i = 0; i <= C; i++) H[i] = __fsub_rn(H[i], R);
         s.cold->frame += (double)R;
     }
 }
 
 template <int C, bool MIXED, bool FULLW>
-__device__ __forceinline__ void wband_loop(WLane<C> &s, const ReadCtx &r, float (&P)[C], float (&PP)[C])
+__device__ __forceinline__ void wband_loop(WLane<C> &s, const ReadCtx &r, float (&P)[C + 1], float (&H)[C + 1])
 {
     const int b_end = r.n_e + r.n_k;
     while (s.b <= b_end) {
@@ -1083,11 +1092,11 @@ __device__ __forceinline__ void wband_loop(WLane<C> &s, const ReadCtx &r, float 
             const int to_renorm = (kRenormPeriod - (s.b % kRenormPeriod)) % kRenormPeriod + 1;
             const int m = min(n, to_renorm);
             s.cold->lean_bands += m;
-            wlean_run<C, MIXED, FULLW>(s, r, P, PP, m);
-            if (((s.b - 1) % kRenormPeriod) == 0) wrenormalise<C>(s, r, P, PP);
+            wlean_run<C, MIXED, FULLW>(s, r, P, H, m);
+            if (((s.b - 1) % kRenormPeriod) == 0) wrenormalise<C>(s, r, P, H);
         } else {
-            wband_step<C, MIXED, FULLW>(s, r, P, PP);
-            swap_bands(P, PP);
+            wband_step<C, MIXED, FULLW>(s, r, P, H);
+            swap_bands(P, H);
         }
     }
     cp_async_wait<0>();
@@ -1122,7 +1131,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 
     const int W = a.W, half = W / 2;
     WLane<C> s;
-    float P[C], PP[C];
+    float P[C + 1], H[C + 1];
     // bands 0 and 1: the origin (-1,-1) at offset W/2 of band 0 (score 0);
     // band 1 = band 0 moved by one event, the trim cell (0,-1) at offset W/2.
     s.ll_e = half;
@@ -1130,7 +1139,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 #pragma unroll
     for (int i = 0; i < C; i++) {
         const int j = C * lane + i;
-        PP[i] = (j == half) ? 0.0f : neg_inf();
+        H[i] = (j == half) ? 0.0f : neg_inf();
         P[i] = (j == half) ? d.lp_trim : neg_inf();
         s.X[i] = event_value(r.ev, s.ll_e - j, r.n_e);
         const float4 q = above ? no_kmer() : kmer_operands(r.kc, s.ll_k + j, r.n_k);
@@ -1138,10 +1147,10 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
         s.B[i] = q.y;
         s.Cc[i] = q.z;
     }
-    // band 1's shifted view of band 0 (band 1 moved by one event)
-    s.qprev = __shfl_sync(kFull, PP[C - 1], r.src_up);
-    if (r.first_lane) s.qprev = neg_inf();
-    s.kprev = false;
+    P[C] = neg_inf();
+    // band 1's view of band 0 (band 1 moved by one event): Q = {boundary, S_0[0..C-1]}
+    H[C] = __shfl_sync(kFull, H[C - 1], r.src_up);
+    if (r.first_lane) H[C] = neg_inf();
     s.ring = rings;
     s.k_req = s.ll_k + r.Wp;
     s.e_req = s.ll_e + 1;
@@ -1166,7 +1175,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     cold.cells = 0;
     cold.lean_bands = 0;
 
-    wband_loop<C, MIXED, FULLW>(s, r, P, PP);
+    wband_loop<C, MIXED, FULLW>(s, r, P, H);
 
     // end cell: max score, then smallest event (the first maximum in event order)
     double best = cold.best;
