@@ -58,9 +58,11 @@ EXTRA_WORKLOADS = ("batch_4096_ln5kb", "wide_10k_ln10kb_k9_w200")
 DEPTH = {"large_50k_ln8kb": 2, "batch_4096_ln5kb": 6, "wide_10k_ln10kb_k9_w200": 2}
 METRIC = "ABEA band-cell updates/s (GCUPS) and reads/s on 1 GB300; p50/p99 latency served"
 UNIT = "GCUPS"
-# Issue slots of one cell update in the canonical form (the roofline's unit of work): 2 FFMA (emission),
-# 4 FADD, 2 compares and 2 selects (the two maxima with their directions), 2 votes (the 2-bit trace) and
-# 2 for the band's bookkeeping shared over its cells.
+# Issue slots of one cell update, the roofline's unit of work: 14, the budget of the canonical op sequence
+# (10 FP32-pipe ops: x - mu', times 1/sigma', the emission, 5 FADD and 2 maxima; about 4 more for the
+# 2-bit trace).  The kernel's own sequence is shorter (2 FFMA, 3 FADD, 2 compares and 2 selects for the
+# two maxima with their directions, 2 votes for the trace, plus the band's bookkeeping shared over its
+# cells), so the fraction quoted against 14 is the conservative one.
 OPS_PER_CELL = 14
 # DRAM bytes (read + write) per band of the core kernel from one ncu capture, valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.

@@ -12,7 +12,10 @@
  *   -DORACLE_F32       FP32 scoring in the canonical single-precision form
  *                      that the GPU path also uses (see cell_score below),
  *                      so that both make every max/argmax decision on the
- *                      same FP32 values.
+ *                      same FP32 values.  In this form every cell carries
+ *                      T = S + lp_step (S the paper's score), which makes
+ *                      the diagonal candidate T_diag itself; the reported
+ *                      score subtracts lp_step again in FP64.
  * Build with -ffp-contract=off: no multiply-add may be fused unless written
  * as fma()/fmaf().
  *
@@ -122,6 +125,7 @@ void oracle_constants(int32_t n_events, int32_t n_kmers, double *out);
 typedef struct {
     real lp_skip, lp_stay, lp_step, lp_trim;
 #ifdef ORACLE_F32
+    float lp_stay_step;        /* lp_stay - lp_step, FP64 rounded once */
     float *a, *b, *c;          /* per k-mer of the read, see emission() */
 #else
     double *mu, *sigma;        /* per k-mer of the read: scaled mean, scaled stdv */
@@ -133,9 +137,11 @@ typedef struct {
  *   lp = ln(1/sqrt(2pi)) - ln(sigma') - z^2/2
  *      = c - z'^2,   z' = z/sqrt(2) = x*a + b,
  *   a = sqrt(1/2)/sigma',  b = -mu'*a,  c = ln(1/sqrt(2pi)) - ln(sigma').
- * a, b, c are computed per k-mer in FP64 and rounded once to FP32:
+ * The FP32 form returns lp + lp_step (the diagonal transition folded in, see
+ * cell_score).  a, b, c are computed per k-mer in FP64 and rounded once:
  *   a = (sqrt(1/2)/sigma) * (1/var),  b = -(mu' * a_fp64),
- *   c = (ln(1/sqrt(2pi)) - ln(sigma)) - ln(var),   mu' = scale*mean + shift.
+ *   c = (ln(1/sqrt(2pi)) - ln(sigma)) - (ln(var) - lp_step),
+ *   mu' = scale*mean + shift.
  * Then two fused multiply-adds: z' = fmaf(x, a, b), lp = fmaf(-z', z', c). */
 static inline float emission(const read_params *p, float x, int32_t k)
 {
@@ -159,14 +165,18 @@ static inline real cell_score(const read_params *p, real up, real left, real dia
                               real lp_emission, uint8_t *dir, double *margin)
 {
 #ifdef ORACLE_F32
-    /* score_d = diag + lp_step + lp_emission and
-     * score_u = up + lp_stay + lp_emission share lp_emission, so
-     * max(score_d, score_u) = max(diag + lp_step, up + lp_stay) + lp_emission.
-     * Rounding is monotone, so this equals the max of the two separately
-     * rounded FP32 sums; the direction is taken on the sums before the
+    /* Every score is carried as T = S + lp_step, and lp_emission here is the
+     * emission plus lp_step.  Then, in exact arithmetic,
+     *   T_d = S_diag + lp_step + E + lp_step = T_diag + lp_emission,
+     *   T_u = S_up + lp_stay + E + lp_step = (T_up + (lp_stay - lp_step)) + lp_emission,
+     *   T_l = S_left + lp_skip + lp_step = T_left + lp_skip,
+     * and the diagonal candidate needs no addition.  T_d and T_u share
+     * lp_emission, so max(T_d, T_u) = max(T_diag, T_up + (lp_stay - lp_step))
+     * + lp_emission; rounding is monotone, so this equals the max of the two
+     * separately rounded FP32 sums, and the direction is taken before the
      * emission is added (D on ties). */
-    real d = diag + p->lp_step;
-    real u = up + p->lp_stay;
+    real d = diag;
+    real u = up + p->lp_stay_step;
     real m;
     uint8_t t;
     if (u > d) { m = u; t = TR_U; } else { m = d; t = TR_D; }
@@ -228,15 +238,16 @@ static int setup_read(const float *model_mean, const float *model_stdv, int32_t 
     p->b = (float *)malloc(sizeof(float) * (size_t)n_k);
     p->c = (float *)malloc(sizeof(float) * (size_t)n_k);
     if (!p->a || !p->b || !p->c) { free(ranks); return ST_NOMEM; }
+    p->lp_stay_step = (float)(c[1] - c[2]);
     double dscale = scale, dshift = shift, dvar = var;
-    double inv_var = 1.0 / dvar, log_var = log(dvar);
+    double inv_var = 1.0 / dvar, log_var_step = log(dvar) - c[2];
     for (int32_t i = 0; i < n_k; i++) {
         double mean = model_mean[ranks[i]], sd = model_stdv[ranks[i]];
         double mu_p = dscale * mean + dshift;
         double a = (SQRT_HALF / sd) * inv_var;
         p->a[i] = (float)a;
         p->b[i] = (float)(-(mu_p * a));
-        p->c[i] = (float)((LOG_INV_SQRT_2PI - log(sd)) - log_var);
+        p->c[i] = (float)((LOG_INV_SQRT_2PI - log(sd)) - log_var_step);
     }
 #else
     p->mu = (double *)malloc(sizeof(double) * (size_t)n_k);
@@ -354,6 +365,10 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
     SCORE(0, half) = 0;
     SCORE(1, ll_e[1] - 0) = p.lp_trim;          /* cell (0,-1) */
     TRACE(1, ll_e[1] - 0) = TR_U;
+#ifdef ORACLE_F32
+    SCORE(0, half) += p.lp_step;                /* T = S + lp_step */
+    SCORE(1, ll_e[1] - 0) += p.lp_step;
+#endif
 
     for (int64_t b = 2; b < n_bands; b++) {
         /* suzuki_kasahara_rule on the previous band's two end cells */
@@ -385,6 +400,9 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
             int32_t e = ll_e[b] - jt;
             if (e >= 0 && e < n_e) {
                 SCORE(b, jt) = (real)(e + 1) * p.lp_trim;
+#ifdef ORACLE_F32
+                SCORE(b, jt) += p.lp_step;
+#endif
                 TRACE(b, jt) = TR_U;
             }
         }
@@ -448,7 +466,11 @@ int NAME(oracle_abea)(const float *model_mean, const float *model_stdv, int32_t 
     if (best != -INFINITY && second != -INFINITY && best - second < min_margin)
         min_margin = best - second;
 #endif
-    res->score = (double)(real)best;
+#ifdef ORACLE_F32
+    res->score = (double)(float)(best - (double)p.lp_step);   /* S = T - lp_step, in FP64 */
+#else
+    res->score = best;
+#endif
     res->e_end = e_best;
 
     if (best == -INFINITY) {
@@ -536,6 +558,10 @@ int NAME(oracle_full_dp)(const float *model_mean, const float *model_stdv, int32
     for (int64_t i = 0; i < R * C; i++) { S[i] = -INFINITY; T[i] = TR_D; }
     FS(-1, -1) = 0;
     for (int32_t e = 0; e < n_e; e++) { FS(e, -1) = (real)(e + 1) * p.lp_trim; FT(e, -1) = TR_U; }
+#ifdef ORACLE_F32
+    FS(-1, -1) += p.lp_step;                    /* T = S + lp_step */
+    for (int32_t e = 0; e < n_e; e++) FS(e, -1) += p.lp_step;
+#endif
     for (int32_t e = 0; e < n_e; e++)
         for (int32_t kk = 0; kk < n_k; kk++) {
             uint8_t dir;
@@ -550,7 +576,11 @@ int NAME(oracle_full_dp)(const float *model_mean, const float *model_stdv, int32
         real cand = FS(e, n_k - 1) + (real)(n_e - 1 - e) * p.lp_trim;
         if (cand > best) { best = cand; e_best = e; }
     }
+#ifdef ORACLE_F32
+    res->score = (double)(float)((double)best - (double)p.lp_step);   /* S = T - lp_step, in FP64 */
+#else
     res->score = best;
+#endif
     res->e_end = e_best;
     if (best == -INFINITY) {
         res->status = ST_FAIL_NO_END;

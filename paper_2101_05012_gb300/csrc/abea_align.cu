@@ -56,12 +56,16 @@
 //     the lanes and stored 32 at a time.
 //
 // All FP32 arithmetic uses explicitly rounded intrinsics, so no operation is
-// fused or reordered: the scores equal those of the FP32 canonical form
-//   z = fmaf(x, a, b); E = fmaf(-z, z, c);
-//   d = diag + lp_step; u = up + lp_stay; m = (u > d) ? u : d; s = m + E;
-//   l = left + lp_skip; S = (l > s) ? l : s
-// (max(diag+lp_step+E, up+lp_stay+E) = max(diag+lp_step, up+lp_stay) + E
-// because rounding is monotone), plus the exact renormalisation below.
+// fused or reordered: the scores equal those of the FP32 canonical form,
+// in which every cell carries T = S + lp_step (S the recurrence's score):
+//   z = fmaf(x, a, b); E' = fmaf(-z, z, c'), c' = c + lp_step (E' = E + lp_step);
+//   d = diag; u = up + (lp_stay - lp_step); m = (u > d) ? u : d; s = m + E';
+//   l = left + lp_skip; T = (l > s) ? l : s
+// (in exact arithmetic T_d = S_diag + lp_step + E + lp_step = T_diag + E',
+// T_u = T_up + (lp_stay - lp_step) + E', T_l = T_left + lp_skip; and
+// max(d + E', u + E') = max(d, u) + E' because rounding is monotone).  The
+// origin scores lp_step, the trim column (e+1)*lp_trim + lp_step, and the
+// end score subtracts lp_step in FP64.  Plus the exact renormalisation below.
 #include <algorithm>
 #include <climits>
 
@@ -85,16 +89,17 @@ __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); 
 __device__ __forceinline__ float pos_inf() { return __int_as_float(0x7f800000); }
 
 struct Consts {
-    float lp_skip, lp_stay, lp_step, lp_trim;
+    float lp_skip, lp_stay_step, lp_step, lp_trim;   // lp_stay_step = lp_stay - lp_step
 };
 
+// One cell in the T = S + lp_step form (c includes lp_step).
 __device__ __forceinline__ float cell(float up, float left, float diag, float x, float a, float b, float c,
-                                      float lp_step, float lp_stay, float lp_skip, bool &p0, bool &p1)
+                                      float lp_stay_step, float lp_skip, bool &p0, bool &p1)
 {
     const float z = __fmaf_rn(x, a, b);
     const float em = __fmaf_rn(-z, z, c);
-    const float d = __fadd_rn(diag, lp_step);
-    const float u = __fadd_rn(up, lp_stay);
+    const float d = diag;
+    const float u = __fadd_rn(up, lp_stay_step);
     p0 = u > d;
     const float m = p0 ? u : d;
     const float s = __fadd_rn(m, em);
@@ -219,7 +224,7 @@ __device__ __forceinline__ void band_fill(Lane<C> &s, const ReadCtx &r, float (&
         if (KP) diag = (t == C) ? s.qprev : PP[t < C ? t : 0];
         else diag = (t == 0) ? s.qprev : PP[t > 0 ? t - 1 : 0];
         bool p0, p1;
-        S[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
+        S[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_stay_step, r.lsk, p0, p1);
         if (!FULLW && i == 0) p0 = r.lane31 ? KM : p0;     // the band's move, bit 31 of word 0
         w[2 * i] = __ballot_sync(kFull, p0);
         w[2 * i + 1] = __ballot_sync(kFull, p1);
@@ -433,11 +438,12 @@ __device__ __forceinline__ void band_step(Lane<C> &s, const ReadCtx &r, float (&
             if (r.dead_mask & (1u << i)) PP[i] = neg_inf();
     }
     if (GENERAL) {
-        // trim state: the cell (e,-1) scores (e+1)*lp_trim
+        // trim state: the cell (e,-1) scores (e+1)*lp_trim (+ lp_step in the T form)
         if (s.ll_k < 0) {
             const int jt = -1 - s.ll_k;
             const int e = s.ll_e - jt;
-            const float v = (e >= 0 && e < r.n_e) ? __fmul_rn((float)(e + 1), r.cs.lp_trim) : neg_inf();
+            const float v = (e >= 0 && e < r.n_e) ? __fadd_rn(__fmul_rn((float)(e + 1), r.cs.lp_trim), r.cs.lp_step)
+                                                   : neg_inf();
 #pragma unroll
             for (int i = 0; i < C; i++)
                 if ((GROUP ? r.off0 : 0) + C * r.lane + i == jt && (!GROUP || r.lane < r.L)) PP[i] = v;
@@ -707,8 +713,8 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int2 *stage, int e_en
         const uint32_t *rec = bufs + base * R;
         int2 *sp = stage;
         // One step of the walk.  A cell outside its band (it cannot happen) is noted at the end of
-        // the chunk from the largest offset seen; the load index stays inside the record either way.
-        unsigned jmax = 0;
+        // each chunk from the offset of the cell the walk continues from; the load index stays inside
+        // the record either way.
         auto step = [&]() {
             const int j = le - e;
             unsigned pair, bit;
@@ -722,16 +728,14 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int2 *stage, int e_en
                 pair = (unsigned)j % C;
                 bit = (unsigned)j / C;
             }
-            jmax = max(jmax, (unsigned)j);
             const uint2 w = *reinterpret_cast<const uint2 *>(rec + off * R + 2 * pair);
             const unsigned l = (w.y >> bit) & 1u;
             const unsigned d = (((w.x >> bit) | l) & 1u) ^ 1u;      // D: neither L nor U
             const unsigned ev = __funnelshift_r(em_lo, em_hi, off);  // bit 0: band top-off, bit 1: the one below
             le -= (int)((ev & 1u) + ((ev >> 1) & d));
             *sp++ = make_int2(e, k);
-            const unsigned de = l ^ 1u, dk = l | d;                 // U or D: e-1; L or D: k-1
-            e -= (int)de;
-            k -= (int)dk;
+            e += (int)l - 1;                                         // U or D: e-1
+            k -= (int)(l + d);                                       // L or D: k-1 (L and D exclusive)
             off += 1 + (int)d;
         };
         while (off <= kChunk - 4 && e >= 1 && k >= 1) {      // two steps stay in the chunk and the matrix
@@ -739,7 +743,7 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int2 *stage, int e_en
             step();
         }
         while (off < kChunk && (e | k) >= 0) step();         // at most 32 steps in all per chunk
-        bad |= jmax >= (unsigned)r.W;
+        bad |= (unsigned)(le - e) >= (unsigned)r.W && (e | k) >= 0;
         const int nb = (int)(sp - stage);
         __syncwarp();
         if (r.lane < nb) {             // the chunk's pairs, one per lane
@@ -924,7 +928,7 @@ __device__ __forceinline__ void wband_fill(WLane<C> &s, const ReadCtx &r, float 
         // diag = band b-1's Q at t = i + KM, stored at H[(t + C) mod (C+1)]
         const float diag = KM ? H[i] : H[i == 0 ? C : i - 1];
         bool p0, p1;
-        H[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_step, r.cs.lp_stay, r.lsk, p0, p1);
+        H[i] = cell(up, left, diag, s.X[i], s.A[i], s.B[i], s.Cc[i], r.cs.lp_stay_step, r.lsk, p0, p1);
         w[2 * i] = __ballot_sync(kFull, p0);
         w[2 * i + 1] = __ballot_sync(kFull, p1);
     }
@@ -1010,11 +1014,12 @@ __device__ __forceinline__ void wband_step(WLane<C> &s, const ReadCtx &r, float 
     if (K) s.ll_k++;
     else s.ll_e++;
     wkill_dead<C, MIXED>(r, H);
-    // trim state: the cell (e,-1) scores (e+1)*lp_trim
+    // trim state: the cell (e,-1) scores (e+1)*lp_trim (+ lp_step in the T form)
     if (s.ll_k < 0) {
         const int jt = -1 - s.ll_k;
         const int e = s.ll_e - jt;
-        const float v = (e >= 0 && e < r.n_e) ? __fmul_rn((float)(e + 1), r.cs.lp_trim) : neg_inf();
+        const float v = (e >= 0 && e < r.n_e) ? __fadd_rn(__fmul_rn((float)(e + 1), r.cs.lp_trim), r.cs.lp_step)
+                                                   : neg_inf();
 #pragma unroll
         for (int i = 0; i < C; i++)
             if (C * r.lane + i == jt) H[i] = v;
@@ -1125,7 +1130,7 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 #pragma unroll
     for (int i = 0; i < C; i++)
         if (C * lane + i >= a.W) r.dead_mask |= 1u << i;
-    r.cs = Consts{d.lp_skip, d.lp_stay, d.lp_step, d.lp_trim};
+    r.cs = Consts{d.lp_skip, d.lp_stay_step, d.lp_step, d.lp_trim};
     const bool above = lane >= a.L;                 // a lane above the band
     r.lsk = above ? neg_inf() : d.lp_skip;
 
@@ -1139,8 +1144,8 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
 #pragma unroll
     for (int i = 0; i < C; i++) {
         const int j = C * lane + i;
-        H[i] = (j == half) ? 0.0f : neg_inf();
-        P[i] = (j == half) ? d.lp_trim : neg_inf();
+        H[i] = (j == half) ? d.lp_step : neg_inf();                        // origin: S = 0
+        P[i] = (j == half) ? __fadd_rn(d.lp_trim, d.lp_step) : neg_inf();  // (0,-1): S = lp_trim
         s.X[i] = event_value(r.ev, s.ll_e - j, r.n_e);
         const float4 q = above ? no_kmer() : kmer_operands(r.kc, s.ll_k + j, r.n_k);
         s.A[i] = q.x;
@@ -1214,7 +1219,9 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     }
     if (lane == 0) {
         abea_result res;
-        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY) ? __double2float_rn(best) : neg_inf();
+        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY)
+                        ? __double2float_rn(best - (double)d.lp_step)    // S = T - lp_step
+                        : neg_inf();
         res.status = status;
         res.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
         res.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : best_e;
@@ -1273,7 +1280,7 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
 #pragma unroll
     for (int i = 0; i < C; i++)
         if (C * lane + i >= Wg) r.dead_mask |= 1u << i;
-    r.cs = Consts{d.lp_skip, d.lp_stay, d.lp_step, d.lp_trim};
+    r.cs = Consts{d.lp_skip, d.lp_stay_step, d.lp_step, d.lp_trim};
     const bool live = lane < Lg;
     r.lsk = live ? d.lp_skip : neg_inf();
     r.off0 = warp * Wg;
@@ -1283,13 +1290,14 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
 
     Lane<C> s;
     float P[C], PP[C];
+    const float t_origin = d.lp_step, t_trim0 = __fadd_rn(d.lp_trim, d.lp_step);   // T = S + lp_step
     s.ll_e = half;
     s.ll_k = -1 - half;
 #pragma unroll
     for (int i = 0; i < C; i++) {
         const int j = r.off0 + C * lane + i;
-        PP[i] = (live && j == half) ? 0.0f : neg_inf();
-        P[i] = (live && j == half) ? d.lp_trim : neg_inf();
+        PP[i] = (live && j == half) ? t_origin : neg_inf();
+        P[i] = (live && j == half) ? t_trim0 : neg_inf();
         s.X[i] = event_value(r.ev, s.ll_e - j, r.n_e);
         const float4 q = live ? kmer_operands(r.kc, s.ll_k + j, r.n_k) : no_kmer();
         s.A[i] = q.x;
@@ -1297,10 +1305,10 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
         s.Cc[i] = q.z;
     }
     // band 1's shifted view of band 0 (S_0 one offset below the lane's first slot)
-    s.qprev = (live && r.off0 + C * lane - 1 == half) ? 0.0f : neg_inf();
+    s.qprev = (live && r.off0 + C * lane - 1 == half) ? t_origin : neg_inf();
     // the neighbour warps' edges of band 1 (its only finite cell is at offset W/2)
-    s.nb_lo = (warp > 0 && r.off0 - 1 == half) ? d.lp_trim : neg_inf();
-    s.nb_hi = (warp < kWarps - 1 && r.off0 + Wg == half) ? d.lp_trim : neg_inf();
+    s.nb_lo = (warp > 0 && r.off0 - 1 == half) ? t_trim0 : neg_inf();
+    s.nb_hi = (warp < kWarps - 1 && r.off0 + Wg == half) ? t_trim0 : neg_inf();
     s.kprev = false;
     s.ev_base = s.ll_e + 1 - r.off0;
     s.ev_cur = event_value(r.ev, s.ev_base + lane, r.n_e);
@@ -1311,7 +1319,7 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
     next_event(s, r, s.ll_e + 1 - r.off0);
     next_kmer(s, r, s.ll_k + r.off0 + Wg);
     s.b = 1;
-    s.knext = general_move<C>(s, r, (half == 0) ? d.lp_trim : neg_inf(), (half == W - 1) ? d.lp_trim : neg_inf());
+    s.knext = general_move<C>(s, r, (half == 0) ? t_trim0 : neg_inf(), (half == W - 1) ? t_trim0 : neg_inf());
     s.b = 2;
     Cold cold;
     s.cold = &cold;
@@ -1378,7 +1386,9 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
     }
     if (lane == 0) {
         abea_result res;
-        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY) ? __double2float_rn(best) : neg_inf();
+        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY)
+                        ? __double2float_rn(best - (double)d.lp_step)    // S = T - lp_step
+                        : neg_inf();
         res.status = status;
         res.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
         res.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : best_e;

@@ -188,13 +188,13 @@ int plan_reads(const abea_ctx *c, const Geometry &g, const std::vector<int32_t> 
             const double lp_step = std::log(1.0 - std::exp(lp_skip) - std::exp(lp_stay));
             const double lp_trim = std::log(1.0 / 100.0);
             d.lp_skip = (float)lp_skip;
-            d.lp_stay = (float)lp_stay;
+            d.lp_stay_step = (float)(lp_stay - lp_step);
             d.lp_step = (float)lp_step;
             d.lp_trim = (float)lp_trim;
             d.scale = (double)s.scale;
             d.shift = (double)s.shift;
             d.inv_var = 1.0 / (double)s.var;
-            d.log_var = std::log((double)s.var);
+            d.log_var_step = std::log((double)s.var) - lp_step;
             const Footprint f = footprint(n_e, n_k, g);
             d.kc_off = (int64_t)total.kc;
             d.tr_off = (int64_t)total.trace;

@@ -23,8 +23,12 @@ struct ReadDesc {
     int32_t n_k;        // k-mers
     int32_t pair_cap;   // output pair capacity
     int32_t host_bad;   // rejected on the host (counts, scalings)
-    float lp_skip, lp_stay, lp_step, lp_trim;   // transition constants, FP64 rounded once
-    double scale, shift, inv_var, log_var;      // read-model scaling, FP64
+    // transition constants, FP64 rounded once; lp_stay_step = lp_stay - lp_step (the scores are
+    // carried as S + lp_step, so the stay transition adds lp_stay - lp_step)
+    float lp_skip, lp_stay_step, lp_step, lp_trim;
+    // read-model scaling, FP64; log_var_step = ln(var) - lp_step (folds lp_step into the k-mer
+    // cache's emission constant)
+    double scale, shift, inv_var, log_var_step;
 };
 static_assert(sizeof(ReadDesc) == 112, "descriptor layout");
 

@@ -169,13 +169,13 @@ extern "C" int abea_align_batch_device_noalloc(int k, const float *level_mean, c
             const double lp_stay = std::log(1.0 - 1.0 / (epk + 1.0));
             const double lp_step = std::log(1.0 - std::exp(lp_skip) - std::exp(lp_stay));
             d.lp_skip = (float)lp_skip;
-            d.lp_stay = (float)lp_stay;
+            d.lp_stay_step = (float)(lp_stay - lp_step);
             d.lp_step = (float)lp_step;
             d.lp_trim = (float)std::log(1.0 / 100.0);
             d.scale = (double)s.scale;
             d.shift = (double)s.shift;
             d.inv_var = 1.0 / (double)s.var;
-            d.log_var = std::log((double)s.var);
+            d.log_var_step = std::log((double)s.var) - lp_step;
             const int64_t bands = n_e + n_k + 1;
             d.kc_off = (int64_t)ckc;
             d.tr_off = (int64_t)ctr;

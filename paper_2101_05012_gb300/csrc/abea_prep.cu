@@ -9,8 +9,10 @@
 //   a = sqrt(1/2)/sigma',  b = -mu'*a,  c = ln(1/sqrt(2 pi)) - ln(sigma'),
 // so that the emission of Alg. adaptivebandedcpucomputelog is
 //   ln(1/sqrt(2 pi)) - ln(sigma') - ((x-mu')/sigma')^2/2 = c - (x*a + b)^2.
-// a, b, c are formed in FP64 (explicitly rounded operations, never fused)
-// and rounded once to FP32.  The same kernel checks the read's bases and
+// The core kernel carries every score as S + lp_step, so its c also holds
+// the read's lp_step (the diagonal transition): c = (ln(1/sqrt(2 pi)) -
+// ln(stdv)) - (ln(var) - lp_step).  a, b, c are formed in FP64 (explicitly
+// rounded operations, never fused) and rounded once to FP32.  The same kernel checks the read's bases and
 // events and flags the read when one is invalid.
 #include "abea_internal.h"
 
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const ReadDesc *__restrict__ 
             const double mu_p = __dadd_rn(__dmul_rn(d.scale, m.mu), d.shift);
             const double a = __dmul_rn(m.a0, d.inv_var);
             const double b = -__dmul_rn(mu_p, a);
-            const double c = __dsub_rn(m.c0, d.log_var);
+            const double c = __dsub_rn(m.c0, d.log_var_step);
             out[i] = make_float4(__double2float_rn(a), __double2float_rn(b), __double2float_rn(c), 0.0f);
         }
         const float *ev = events + d.ev_off;
