@@ -66,7 +66,7 @@ UNIT = "GCUPS"
 OPS_PER_CELL = 14
 # DRAM bytes (read + write) per band of the core kernel from one ncu capture, valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.
-TRAFFIC_CAPTURE = {"source_sha1": None, "bytes_per_band": None}
+TRAFFIC_CAPTURE = {"source_sha1": "5a93bc4c74ff95fcca84bad78286168669f69d1b", "bytes_per_band": 85.622}
 
 
 def parse():
@@ -563,6 +563,7 @@ def run_ours(args):
                        "W": xb.W, "k": xb.k, "cells_per_step": x.cells, "gpu_launches": xl,
                        "kernel": kernel_name(xb.W)}
         if name == "batch_4096_ln5kb":
+            extra[name]["autotune"] = autotune_leg(x)
             scal_line, ea_line, ev_line = secondary_kernels(torch, binding, synth, x, args)
         x.close()
 
@@ -603,6 +604,24 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def autotune_leg(x):
+    """abea_autotune on a sample of the batch (its 32 longest reads and every 16th read), then the
+    one-batch latency with the tuned launch geometry against per-warp mode alone (context 0)."""
+    b, ctx = x.batch, x.ctxs[0]
+    bands = b.n_events().astype(np.int64) + np.maximum(b.n_kmers(), 1) + 1
+    ids = np.unique(np.concatenate([np.argsort(-bands)[:32], np.arange(0, b.n, 16)]))
+    t0 = time.perf_counter()
+    choices = ctx.autotune(b.subset(ids))
+    tune_s = time.perf_counter() - t0
+    tuned = x.latency()
+    ctx.set_block_mode(0.0)                     # back to per-warp mode for the legs after this one
+    per_warp = x.latency()
+    return {"sample_reads": int(len(ids)), "tune_s": tune_s,
+            "choices": [{k: (int(c[k]) if k not in ("gcups_per_warp", "gcups_block") else float(c[k]))
+                         for k in c.dtype.names} for c in choices],
+            "batch_latency_ms_tuned": tuned, "batch_latency_ms_per_warp": per_warp}
 
 
 def secondary_kernels(torch, binding, synth, x, args):

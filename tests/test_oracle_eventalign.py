@@ -89,3 +89,23 @@ def test_planted_mistakes_fail(mistake):
     else:
         ref_pos = np.array([0, 1, 2, -1, 3, 5, 6], np.int32)
         assert [int(ref_pos[j + 2]) for j in q["kmer"]] != good_ref
+
+
+def test_read_summary_hand_worked():
+    """Read summary of a hand-walked path (reading of eventalign's per-read summary): 8 events,
+    5 k-mers, pairs (1,0) (2,0) (3,1) (3,2) (3,3) (4,4): one stay (2,0), two skips (3,2) (3,3), so
+    4 events aligned; events 0, 5, 6 and 7 trimmed (4 of 8, not more than half); 2 skips, above a
+    fifth of 5 k-mers; score -12 over 8 events = -1.5 per event."""
+    pairs = np.array([(1, 0), (2, 0), (3, 1), (3, 2), (3, 3), (4, 4)], np.int32)
+    s = ea.read_summary(3, 8, 5, 0, -12.0, pairs)[0]
+    assert (s["read"], s["status"], s["n_events"], s["n_kmers"], s["n_pairs"]) == (3, 0, 8, 5, 6)
+    assert (s["first_event"], s["last_event"], s["events_aligned"], s["stays"], s["skips"]) == (1, 4, 4, 1, 2)
+    assert s["score"] == np.float32(-12.0) and s["score_per_event"] == np.float32(-1.5)
+    assert s["flags"] == ea.QC_SKIPS
+    # more than half of the events trimmed and a low score per event; no skip
+    s = ea.read_summary(0, 10, 3, 0, -120.0, np.array([(6, 0), (7, 1), (8, 2)], np.int32))[0]
+    assert (s["stays"], s["skips"], s["events_aligned"]) == (0, 0, 3)
+    assert s["flags"] == ea.QC_TRIMMED | ea.QC_LOW_SCORE
+    # no alignment: flagged, no pairs counted
+    s = ea.read_summary(1, 10, 3, 1, -np.inf, np.zeros((0, 2), np.int32))[0]
+    assert s["flags"] == ea.QC_NOT_ALIGNED and s["n_pairs"] == 0 and s["first_event"] == -1
