@@ -775,17 +775,238 @@ __device__ int backtrack(const ReadCtx &r, uint32_t *bufs, int2 *stage, int e_en
 
 // ---------------------------------------------------------------------------
 
-// Pairs (cap - n .. cap-1 of out) moved to the front, ascending, by the warp.
-__device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lane)
+// Pairs (cap - n .. cap-1 of out) moved to the front, ascending, by the
+// `width` lanes of `mask` (lane index `lane` among them), 4*width pairs at a
+// time: the four loads of a lane are in flight together.  Ascending blocks
+// with all loads before the stores are safe however the two ranges overlap
+// (a store never reaches a pair a later block still has to load).
+__device__ __forceinline__ void compact_pairs(int2 *out, int cap, int n, int lane, int width = 32,
+                                              unsigned mask = 0xffffffffu)
 {
+    __syncwarp(mask);
+    for (int base = 0; base < n; base += 4 * width) {
+        int2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int t = base + u * width + lane;
+            v[u] = (t < n) ? out[cap - n + t] : make_int2(0, 0);
+        }
+        __syncwarp(mask);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int t = base + u * width + lane;
+            if (t < n) out[t] = v[u];
+        }
+        __syncwarp(mask);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-warp mode: two walks at once.
+//
+// A warp walks the reads it aligned two at a time, half a warp each: lanes
+// 0-15 walk one read and lanes 16-31 the other, so every instruction of the
+// walk's dependent chain serves two reads.  The walk of a read waits in
+// shared memory (a WalkJob) until the warp has finished the bands of its
+// next read.  The halves run their chunks in step (the same iteration of the
+// chunk loop); a half whose walk has ended idles until the other's ends.
+
+// What the walk of one read needs, from its band loop to its walk.
+struct WalkJob {
+    double best;                     // the end cell's score (T form, renormalisation frame included)
+    long long cells;
+    const uint32_t *tr;              // the read's trace records
+    const uint8_t *mv;               // its per-band move bytes (all 32 lanes live)
+    int2 *out;                       // its pair slot
+    int rid, best_e, best_le, n_k, cap;
+    float lp_step;
+};
+
+// Copy the records of bands top-t (t = 0..31) into buf, lanes hl and hl+16
+// of a half each copying one band's record (nothing when !live).
+template <int R>
+__device__ __forceinline__ void chunk_copy2(const uint32_t *tr, int top, uint32_t *buf, int hl, bool live)
+{
+#pragma unroll
+    for (int rep = 0; rep < 2; rep++) {
+        const int t = hl + 16 * rep;
+        const int mb = top - t;
+        if (live && mb >= 2) {         // bands 0 and 1 hold no matrix cell
+            const uint32_t *src = tr + (size_t)mb * R;
+            uint32_t *dst = buf + t * R;
+#pragma unroll
+            for (int q = 0; q < R / 4; q++) cp_async16(dst + 4 * q, src + 4 * q);
+        }
+    }
+    cp_async_commit();
+}
+
+// Bit t: band top-t moved by one event (this half's chunk).  Both halves call
+// it in step (two ballots over the warp).
+template <int R, bool FULLW>
+__device__ __forceinline__ unsigned chunk_event_moves2(const uint8_t *mv, int top, const uint32_t *buf, int h, int hl,
+                                                       bool live)
+{
+    bool em[2];
+#pragma unroll
+    for (int rep = 0; rep < 2; rep++) {
+        const int t = hl + 16 * rep;
+        const int mb = top - t;
+        bool kmove = false;
+        if (live && mb >= 2) kmove = FULLW ? (mv[mb] != 0) : (((buf[t * R] >> 31) & 1u) != 0);
+        em[rep] = live && mb >= 2 && !kmove;
+    }
+    const unsigned b0 = __ballot_sync(kFull, em[0]) >> (16 * h);
+    const unsigned b1 = __ballot_sync(kFull, em[1]) >> (16 * h);
+    return (b0 & 0xffffu) | ((b1 & 0xffffu) << 16);
+}
+
+// Walk the job at byte offset ja of the kernel's shared memory with lanes
+// 0-15 and the job at jb (-1: none) with lanes 16-31, each as backtrack does
+// for one read (pairs from the end of the read's slot, then moved to the
+// front), and write both results.  The two rings of 3*kChunk records of R
+// words start at word bufs, the two stages of kChunk pairs at byte stages.
+// Out of line: called once per two reads, and its registers then do not
+// weigh on the band loop's allocation; its shared-memory addresses are
+// offsets into the kernel's shared array, so its loads and stores stay
+// shared-memory ones.
+template <int C, int R, bool FULLW>
+__device__ __noinline__ void walk2(int ja, int jb, int W, int bufs, int stages, abea_result *res, int lane)
+{
+    constexpr int RING = 3 * kChunk;
+    const int h = lane >> 4, hl = lane & 15;
+    const unsigned hmask = 0xffffu << (16 * h);
+    const bool live = (h == 0) || (jb >= 0);
+    const WalkJob &j = *reinterpret_cast<const WalkJob *>(reinterpret_cast<const char *>(abea_smem) +
+                                                          ((h == 0 || jb < 0) ? ja : jb));
+    uint32_t *ring = abea_smem + bufs + h * RING * R;
+    int2 *stage = reinterpret_cast<int2 *>(reinterpret_cast<char *>(abea_smem) + stages) + h * kChunk;
+    const uint32_t *tr = j.tr;
+    const uint8_t *mv = j.mv;
+    int2 *out = j.out;
+    const int cap = j.cap;
+    int e = j.best_e, k = j.n_k - 1;
+    int top = e + k + 2;               // band held in ring slot `base`
+    int base = 0;
+    chunk_copy2<R>(tr, top, ring, hl, live);
+    chunk_copy2<R>(tr, top - kChunk, ring + kChunk * R, hl, live);
+    chunk_copy2<R>(tr, top - 2 * kChunk, ring + 2 * kChunk * R, hl, live);
+    cp_async_wait<1>();
     __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int t = base + lane;
-        int2 v = make_int2(0, 0);
-        if (t < n) v = out[cap - n + t];
+    // bit i: band top-i (em_lo) or top-32-i (em_hi) moved by one event
+    unsigned em_lo = chunk_event_moves2<R, FULLW>(mv, top, ring, h, hl, live);
+    unsigned em_hi = chunk_event_moves2<R, FULLW>(mv, top - kChunk, ring + kChunk * R, h, hl, live);
+    int le = j.best_le;
+    int off = 0;                       // the current cell's band is top - off
+    int n = 0;                         // pairs walked before the current chunk
+    bool bad = false;
+    bool done = !live;                 // this half's walk has ended
+    for (;;) {
+        const uint32_t *rec = ring + base * R;
+        int2 *sp = stage;
+        // One step, as in backtrack (per-warp record layout).
+        auto step = [&]() {
+            const int j2 = le - e;
+            const unsigned pair = (unsigned)j2 % C, bit = (unsigned)j2 / C;
+            const uint2 w = *reinterpret_cast<const uint2 *>(rec + off * R + 2 * pair);
+            const unsigned l = (w.y >> bit) & 1u;
+            const unsigned d = (((w.x >> bit) | l) & 1u) ^ 1u;      // D: neither L nor U
+            const unsigned ev = __funnelshift_r(em_lo, em_hi, off);  // bit 0: band top-off, bit 1: the one below
+            le -= (int)((ev & 1u) + ((ev >> 1) & d));
+            *sp++ = make_int2(e, k);
+            e += (int)l - 1;                                         // U or D: e-1
+            k -= (int)(l + d);                                       // L or D: k-1 (L and D exclusive)
+            off += 1 + (int)d;
+        };
+        if (!done) {
+            while (off <= kChunk - 4 && e >= 1 && k >= 1) {      // two steps stay in the chunk and the matrix
+                step();
+                step();
+            }
+            while (off < kChunk && (e | k) >= 0) step();         // at most 32 steps in all per chunk
+            bad |= (unsigned)(le - e) >= (unsigned)W && (e | k) >= 0;
+        }
+        const int nb = (int)(sp - stage);
         __syncwarp();
-        if (t < n) out[t] = v;
+        for (int t = hl; t < nb; t += 16)                         // the chunk's pairs, two per lane at most
+            if (n + t < cap) out[cap - 1 - (n + t)] = stage[t];
+        n += nb;
+        if (!done && ((e | k) < 0 || bad)) done = true;
+        if (__all_sync(kFull, done)) break;
+        // both halves enter their next chunk
         __syncwarp();
+        const int freed = base;
+        top -= kChunk;
+        off -= kChunk;
+        base += kChunk;
+        base -= (base >= RING) ? RING : 0;
+        em_lo = em_hi;
+        cp_async_wait<0>();
+        __syncwarp();
+        int nxt = base + kChunk;
+        nxt -= (nxt >= RING) ? RING : 0;
+        em_hi = chunk_event_moves2<R, FULLW>(mv, top - kChunk, ring + nxt * R, h, hl, !done);
+        chunk_copy2<R>(tr, top - 2 * kChunk, ring + freed * R, hl, !done);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    if (!live) return;
+    int status = ABEA_READ_OK;
+    if (bad) {
+        status = ABEA_READ_FAIL_NO_END;   // internal inconsistency, reported as no alignment
+        n = 0;
+    } else if (n > cap) {
+        status = ABEA_READ_CAPACITY;
+    } else {                          // pairs (cap - n .. cap-1) moved to the front, ascending, by the half
+        compact_pairs(out, cap, n, hl, 16, hmask);
+    }
+    if (hl == 0) {
+        abea_result rr;
+        rr.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY)
+                       ? __double2float_rn(j.best - (double)j.lp_step)   // S = T - lp_step
+                       : neg_inf();
+        rr.status = status;
+        rr.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
+        rr.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : j.best_e;
+        rr.cells = j.cells;
+        res[j.rid] = rr;
+    }
+}
+
+// One read's walk with the whole warp (backtrack), for a read walked alone.
+template <int C, int R, bool FULLW>
+__device__ __noinline__ void walk1(int ja, int W, int bufs, int stages, abea_result *res, int lane)
+{
+    const WalkJob &j = *reinterpret_cast<const WalkJob *>(reinterpret_cast<const char *>(abea_smem) + ja);
+    ReadCtx r;
+    r.tr = const_cast<uint32_t *>(j.tr);
+    r.mv = const_cast<uint8_t *>(j.mv);
+    r.n_k = j.n_k;
+    r.W = W;
+    r.lane = lane;
+    int n = 0;
+    int status = ABEA_READ_OK;
+    const int rc = backtrack<C, R, FULLW, false>(r, abea_smem + bufs,
+                                                 reinterpret_cast<int2 *>(reinterpret_cast<char *>(abea_smem) + stages),
+                                                 j.best_e, j.best_le, j.out, j.cap, n);
+    if (rc != 0) {
+        status = ABEA_READ_FAIL_NO_END;   // internal inconsistency, reported as no alignment
+        n = 0;
+    } else if (n > j.cap) {
+        status = ABEA_READ_CAPACITY;
+    } else {
+        compact_pairs(j.out, j.cap, n, lane);
+    }
+    if (lane == 0) {
+        abea_result rr;
+        rr.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY)
+                       ? __double2float_rn(j.best - (double)j.lp_step)   // S = T - lp_step
+                       : neg_inf();
+        rr.status = status;
+        rr.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
+        rr.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : j.best_e;
+        rr.cells = j.cells;
+        res[j.rid] = rr;
     }
 }
 
@@ -1107,9 +1328,12 @@ __device__ __forceinline__ void wband_loop(WLane<C> &s, const ReadCtx &r, float 
     cp_async_wait<0>();
 }
 
+// The bands and the end cell of one read.  A read with an end cell leaves
+// its walk in *job (filled by lane 0) and returns true; otherwise its result
+// is written here and it returns false.
 template <int C, bool MIXED, bool FULLW>
-__device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int lane, uint32_t *bt_bufs,
-                           Cold &cold, WRings *rings)
+__device__ bool align_read(const AlignArgs &a, const ReadDesc &d, int rid, int lane, Cold &cold, WRings *rings,
+                           WalkJob *job)
 {
     ReadCtx r;
     r.ev = a.events + d.ev_off;
@@ -1198,36 +1422,33 @@ __device__ void align_read(const AlignArgs &a, const ReadDesc &d, int rid, int l
     }
     const long long cells = cold.cells + cold.lean_bands * (long long)W;   // identical in every lane
 
-    int status = ABEA_READ_OK;
-    int n = 0;
-    int2 *out = reinterpret_cast<int2 *>(a.pairs) + d.pair_off;
-    const int cap = d.pair_cap;
     if (best == -(double)pos_inf()) {
-        status = ABEA_READ_FAIL_NO_END;
-    } else {
-        __syncwarp();                         // lane 0's trace stores are visible to the warp
-        const int rc = backtrack<C, Rec<C>::R, FULLW, false>(r, bt_bufs, reinterpret_cast<int2 *>(rings->k), best_e,
-                                                             best_le, out, cap, n);
-        if (rc != 0) {
-            status = ABEA_READ_FAIL_NO_END;   // internal inconsistency, reported as no alignment
-            n = 0;
-        } else if (n > cap) {
-            status = ABEA_READ_CAPACITY;
-        } else {
-            compact_pairs(out, cap, n, lane);
+        if (lane == 0) {
+            abea_result res;
+            res.score = neg_inf();
+            res.status = ABEA_READ_FAIL_NO_END;
+            res.n_pairs = 0;
+            res.e_end = -1;
+            res.cells = cells;
+            a.res[rid] = res;
         }
+        return false;
     }
     if (lane == 0) {
-        abea_result res;
-        res.score = (status == ABEA_READ_OK || status == ABEA_READ_CAPACITY)
-                        ? __double2float_rn(best - (double)d.lp_step)    // S = T - lp_step
-                        : neg_inf();
-        res.status = status;
-        res.n_pairs = (status == ABEA_READ_FAIL_NO_END) ? 0 : n;
-        res.e_end = (status == ABEA_READ_FAIL_NO_END) ? -1 : best_e;
-        res.cells = cells;
-        a.res[rid] = res;
+        job->best = best;
+        job->cells = cells;
+        job->tr = r.tr;
+        job->mv = r.mv;
+        job->out = reinterpret_cast<int2 *>(a.pairs) + d.pair_off;
+        job->rid = rid;
+        job->best_e = best_e;
+        job->best_le = best_le;
+        job->n_k = d.n_k;
+        job->cap = d.pair_cap;
+        job->lp_step = d.lp_step;
     }
+    __syncwarp();                             // the job and the read's trace stores are visible to the warp
+    return true;
 }
 
 // Shared state of block mode.
@@ -1397,17 +1618,21 @@ __device__ __noinline__ void align_read_group(const AlignArgs &a, const ReadDesc
     }
 }
 
-// Dynamic shared memory layout for per-warp C and block-mode CG: per warp a
-// ring of 3*kChunk records of RB words (RB = the larger record of the two
-// modes), then the block-mode exchange state.
+// Dynamic shared memory layout for per-warp C and block-mode CG: per warp
+// the two walk rings of 3*kChunk records of R words (one per half-warp; in
+// block mode warp 0's region holds the one ring of 3*kChunk block records),
+// the block-mode exchange state, one Cold per thread, one WRings per warp,
+// two WalkJobs per warp.
 template <int C, int CG>
 struct Smem {
-    static constexpr int RB = (CG > 0 && 2 * CG * kWarps > Rec<C>::R) ? 2 * CG * kWarps : Rec<C>::R;
-    static constexpr int GS_WORDS = kWarps * 3 * kChunk * RB;
+    static constexpr int WALK_WORDS = 2 * 3 * kChunk * Rec<C>::R;     // per warp
+    static_assert(CG == 0 || 3 * kChunk * 2 * CG * kWarps <= WALK_WORDS, "block-mode ring fits warp 0's region");
+    static constexpr int GS_WORDS = kWarps * WALK_WORDS;
     static constexpr size_t GS_BYTES = CG > 0 ? (sizeof(GroupShared) + 15) / 16 * 16 : 0;
     static constexpr size_t COLD_OFF = 4 * (size_t)GS_WORDS + GS_BYTES;   // one Cold per thread
     static constexpr size_t RING_OFF = COLD_OFF + kWarps * 32 * sizeof(Cold); // one WRings per warp
-    static constexpr size_t BYTES = RING_OFF + kWarps * sizeof(WRings);
+    static constexpr size_t JOB_OFF = (RING_OFF + kWarps * sizeof(WRings) + 15) / 16 * 16;   // two WalkJobs per warp
+    static constexpr size_t BYTES = JOB_OFF + kWarps * 2 * sizeof(WalkJob);
 };
 
 // Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
@@ -1425,12 +1650,16 @@ struct Occupancy {
 template <int C, bool MIXED, bool FULLW, int CG>
 __global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::blocks) align_kernel(const AlignArgs a)
 {
-    constexpr int RB = Smem<C, CG>::RB;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint32_t *bt = abea_smem + warp * 3 * kChunk * RB;
     Cold &cold = reinterpret_cast<Cold *>(reinterpret_cast<char *>(abea_smem) + Smem<C, CG>::COLD_OFF)[threadIdx.x];
     WRings *rings = reinterpret_cast<WRings *>(reinterpret_cast<char *>(abea_smem) + Smem<C, CG>::RING_OFF) + warp;
+    WalkJob *jobs = reinterpret_cast<WalkJob *>(reinterpret_cast<char *>(abea_smem) + Smem<C, CG>::JOB_OFF) + 2 * warp;
+    // walk2's shared-memory operands as offsets: the jobs, the rings, the stages (the operand ring
+    // is idle while the warp walks)
+    const int job_off = (int)(Smem<C, CG>::JOB_OFF + 2 * warp * sizeof(WalkJob));
+    const int bt_off = warp * Smem<C, CG>::WALK_WORDS;
+    const int stage_off = (int)(Smem<C, CG>::RING_OFF + warp * sizeof(WRings));
     if (CG > 0 && (int)blockIdx.x < a.n_group) {
         const int rid = a.order[blockIdx.x];
         const ReadDesc d = a.rd[rid];
@@ -1449,6 +1678,8 @@ __global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::block
         }
         __syncwarp();
     }
+    bool pending = false;              // jobs[cur ^ 1] holds a walk waiting for the next read's
+    int cur = 0;
     for (;;) {
         int q = 0;
         if (lane == 0) q = atomicAdd(a.queue, 1);
@@ -1468,14 +1699,41 @@ __global__ void __launch_bounds__(kWarps * 32, Occupancy<C, MIXED, FULLW>::block
             }
             continue;
         }
-        align_read<C, MIXED, FULLW>(a, d, rid, lane, bt, cold, rings);
+        // The walk of a read waits for the warp's next read, and the two are walked together, while
+        // the queue holds at least one more read per warp; in the queue's tail a read is walked at
+        // once, so that no read's result waits for another read's bands there.
+        if (align_read<C, MIXED, FULLW>(a, d, rid, lane, cold, rings, jobs + cur)) {
+            if (pending) {
+                walk2<C, Rec<C>::R, FULLW>(job_off + (cur ^ 1) * (int)sizeof(WalkJob), job_off + cur * (int)sizeof(WalkJob),
+                                           a.W, bt_off, stage_off, a.res, lane);
+                pending = false;
+            } else if (q + (int)gridDim.x * kWarps < a.n) {
+                pending = true;
+                cur ^= 1;
+            } else {
+                walk1<C, Rec<C>::R, FULLW>(job_off + cur * (int)sizeof(WalkJob), a.W, bt_off, stage_off, a.res, lane);
+            }
+        }
         __syncwarp();
     }
+    if (pending) walk1<C, Rec<C>::R, FULLW>(job_off + (cur ^ 1) * (int)sizeof(WalkJob), a.W, bt_off, stage_off, a.res, lane);
+}
+
+// Dynamic shared memory above the 48 KB default needs the kernel's opt-in
+// (the wide geometries' two walk rings per warp).
+template <int C, bool MIXED, bool FULLW, int CG>
+cudaError_t opt_in_smem()
+{
+    if (Smem<C, CG>::BYTES <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(align_kernel<C, MIXED, FULLW, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Smem<C, CG>::BYTES);
 }
 
 template <int C, bool MIXED, bool FULLW, int CG>
 int launch_c(const AlignArgs &a, int grid, void *stream)
 {
+    const cudaError_t e = opt_in_smem<C, MIXED, FULLW, CG>();
+    if (e != cudaSuccess) return (int)e;
     align_kernel<C, MIXED, FULLW, CG><<<grid, kWarps * 32, Smem<C, CG>::BYTES, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
@@ -1485,6 +1743,8 @@ int grid_c(int device)
 {
     int sms = 0, per_sm = 0;
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return -1;
+    e = opt_in_smem<C, MIXED, FULLW, CG>();
     if (e != cudaSuccess) return -1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_kernel<C, MIXED, FULLW, CG>, kWarps * 32,
                                                       Smem<C, CG>::BYTES);
