@@ -262,6 +262,15 @@ int abea_detect_events(abea_ctx *ctx, int32_t n, const int16_t *d_raw, const int
  * ABEA_ERR_ARG for n < 0 or a null pointer with n > 0. */
 int abea_f32_from_i64(const int64_t *d_in, int64_t n, float *d_out, void *cuda_stream);
 
+/* The double-to-float rounding that the pre-kernel uses for the k-mer
+ * cache's FP64 operands: d_out[j] = the float nearest to d_in[j], ties to
+ * even, formed from integer operations where the result is a normal float
+ * (the FP64 pipe's conversion otherwise).  Exposed so that it can be checked
+ * against the platform's own conversion.  d_in (double[n]) and d_out
+ * (float[n]) are device pointers; enqueued on cuda_stream.  Returns
+ * ABEA_ERR_ARG for n < 0 or a null pointer with n > 0. */
+int abea_f32_from_f64(const double *d_in, int64_t n, float *d_out, void *cuda_stream);
+
 /* Per-read scalings by the method of moments (thesis Sec. "Read-model
  * scaling": shift and scale are estimated per read before ABEA, which then
  * uses mu * scale + shift; the thesis gives no formula).  For read i, with

@@ -30,7 +30,7 @@ SCALE_OK, SCALE_DEGENERATE, SCALE_BAD_INPUT = range(3)
 EXPORTS = ["abea_create", "abea_destroy", "abea_strerror", "abea_set_model", "abea_align", "abea_align_batch",
            "abea_align_packed", "abea_align_batch_device", "abea_last_launch_stats",
            "abea_set_block_mode", "abea_eventalign", "abea_detect_events", "abea_estimate_scalings", "abea_server_start", "abea_server_submit", "abea_server_poll",
-           "abea_server_stop", "abea_align_batch_device_noalloc", "abea_f32_from_i64", "abea_summarise",
+           "abea_server_stop", "abea_align_batch_device_noalloc", "abea_f32_from_i64", "abea_f32_from_f64", "abea_summarise",
            "abea_eventalign_tsv", "abea_summary_tsv", "abea_autotune"]
 
 
@@ -382,6 +382,13 @@ def f32_from_i64(d_in, d_out, stream=None):
     lib = load()
     _check(lib.abea_f32_from_i64(ctypes.c_void_p(d_in.data_ptr()), ctypes.c_int64(d_in.numel()),
                                  ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(stream)), "abea_f32_from_i64")
+
+
+def f32_from_f64(d_in, d_out, stream=None):
+    """abea_f32_from_f64: d_in float64 and d_out float32 torch CUDA tensors of the same length."""
+    lib = load()
+    _check(lib.abea_f32_from_f64(ctypes.c_void_p(d_in.data_ptr()), ctypes.c_int64(d_in.numel()),
+                                 ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(stream)), "abea_f32_from_f64")
 
 
 def _text(fn, *args) -> str:

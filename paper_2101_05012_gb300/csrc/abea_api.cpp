@@ -890,6 +890,13 @@ int abea_f32_from_i64(const int64_t *d_in, int64_t n, float *d_out, void *cuda_s
     return cuda_err((cudaError_t)abea::launch_f32_from_i64(d_in, n, d_out, cuda_stream));
 }
 
+int abea_f32_from_f64(const double *d_in, int64_t n, float *d_out, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_in || !d_out))) return ABEA_ERR_ARG;
+    if (n == 0) return ABEA_OK;
+    return cuda_err((cudaError_t)abea::launch_f32_from_f64(d_in, n, d_out, cuda_stream));
+}
+
 int abea_estimate_scalings(abea_ctx *c, int32_t n, const uint8_t *d_seq, const int64_t *seq_off,
                            const float *d_events, const int64_t *ev_off, abea_scalings *d_out, int32_t *d_status,
                            void *cuda_stream)

@@ -93,6 +93,7 @@ int launch_events(const int64_t *raw_off, const int64_t *ev_off, const int64_t *
                   int32_t n, int64_t n_tiles, const int16_t *raw, const abea_calib *calib, int window, float tau2,
                   void *scratch, abea_event *out, int32_t *n_ev, void *stream);
 int launch_f32_from_i64(const int64_t *in, int64_t n, float *out, void *stream);
+int launch_f32_from_f64(const double *in, int64_t n, float *out, void *stream);
 int launch_scalings(const int64_t *d_seq_off, const int64_t *d_ev_off, int32_t n, const uint8_t *seq,
                     const float *events, const float2 *model_f, int k, abea_scalings *out, int32_t *status,
                     void *stream);

@@ -332,3 +332,43 @@ def test_large_workload_sample_with_ultra_long_reads(ctx):
         launches, _ = small.last_launch_stats()
     assert launches >= 4
     assert np.array_equal(res, r2) and np.array_equal(pairs, p2)
+
+
+def test_prep_double_to_float_rounding():
+    """The pre-kernel rounds its FP64 k-mer operands to float with integer operations
+    (abea_f32_from_f64): identical to numpy's cast and to the device's own conversion on every
+    binade of the float range, on halfway cases with even and odd kept significands (and one unit
+    above and below), on carries into the exponent and past the largest float, on the
+    subnormal, zero, infinite and NaN inputs that take the conversion instruction, and on the
+    pre-kernel's own operand ranges."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(17)
+    u = []
+    for e in range(1023 - 130, 1023 + 131):
+        m = rng.integers(0, 1 << 23, 400, dtype=np.uint64)
+        for rest in (0x10000000, 0x0FFFFFFF, 0x10000001, 0, 0x1FFFFFFF):
+            u.append((np.uint64(e) << np.uint64(52)) | (m << np.uint64(29)) | np.uint64(rest))
+        u.append((np.uint64(e) << np.uint64(52)) | rng.integers(0, 1 << 52, 2000, dtype=np.uint64))
+        u.append((np.uint64(e) << np.uint64(52)) | (np.uint64(0x7FFFFF) << np.uint64(29)) | np.uint64(0x10000000))
+    u = np.concatenate([np.atleast_1d(x) for x in u])
+    v = u.view(np.float64)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, 1e-310, 3.4028234663852886e38,
+                        3.4028235677973366e38, 1.1754943508222875e-38, 1.1754942e-38], np.float64)
+    # the pre-kernel's operands: a = sqrt(1/2)/sigma', b = -mu'*a, c = ln(1/sqrt(2 pi)) - ln sigma' + lp_step
+    ops = np.concatenate([0.7071067811865476 / rng.uniform(1, 4.5, 20000),
+                          -rng.uniform(50, 150, 20000) * (0.7071067811865476 / rng.uniform(1, 4.5, 20000)),
+                          -0.9189385332046727 - np.log(rng.uniform(1, 4.5, 20000)) + rng.uniform(-2, -0.05, 20000)])
+    v = np.concatenate([v, -v, special, ops])
+    d_in = torch.from_numpy(v).to(dev)
+    d_out = torch.empty(len(v), dtype=torch.float32, device=dev)
+    binding.f32_from_f64(d_in, d_out)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint32)
+    with np.errstate(over="ignore"):
+        want = v.astype(np.float32)
+    nan = np.isnan(want)
+    assert np.array_equal(got[~nan], want[~nan].view(np.uint32))
+    assert np.all(np.isnan(got[nan].view(np.float32)))
+    dev_cast = d_in.to(torch.float32).cpu().numpy()
+    assert np.array_equal(got[~nan], dev_cast[~nan].view(np.uint32))
