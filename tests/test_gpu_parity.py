@@ -372,3 +372,46 @@ def test_prep_double_to_float_rounding():
     assert np.all(np.isnan(got[nan].view(np.float32)))
     dev_cast = d_in.to(torch.float32).cpu().numpy()
     assert np.array_equal(got[~nan], dev_cast[~nan].view(np.uint32))
+
+
+def test_paired_walks_with_rejected_and_short_slots(ctx):
+    """8,000 short reads (far more than the launch's warps), so that most reads are walked two at
+    a time: every 97th read is rejected (a non-ACGT base), every 89th has one pair slot too few,
+    and the lengths vary so that a walk's partner is shorter or longer.  Statuses, scores,
+    end events, cell counts and pairs equal the FP32 oracle's (rejected and short-slot reads by
+    status and pair count)."""
+    rng = np.random.default_rng(21)
+    lengths = rng.integers(150, 700, 8000).tolist()
+    b = _lengths_batch(lengths, seed=13)
+    ev, sq, sc = [], [], []
+    for i in range(b.n):
+        e, s, c = b.read(i)
+        if i % 97 == 5:
+            s = s[:40] + b"N" + s[41:]
+        ev.append(e)
+        sq.append(s)
+        sc.append(c)
+    b = synth.custom_batch(ev, sq, sc, b.model_mean, b.model_stdv, b.k, b.W)
+    o = oracle.abea_batch(b, "f32", n_threads=THREADS)
+    short = np.arange(b.n) % 89 == 3
+    short &= o["status"] == oracle.ST_OK
+    caps = np.maximum(b.n_events() + np.maximum(b.n_kmers(), 1) - 1, 1).astype(np.int64)
+    caps[short] = o["n_pairs"][short] - 1
+    po = np.zeros(b.n + 1, np.int64)
+    np.cumsum(caps, out=po[1:])
+    res, pairs, po = run_gpu(ctx, b, pair_off=po, theta=0.0)
+    rejected = np.arange(b.n) % 97 == 5
+    assert np.all(res["status"][rejected] == binding.READ_BAD_INPUT)
+    assert np.all(res["status"][short] == binding.READ_CAPACITY)
+    assert np.array_equal(res["n_pairs"][short], o["n_pairs"][short])
+    ok = ~rejected & ~short
+    assert np.all(res["status"][ok] == o["status"][ok])
+    bad = []
+    for i in np.nonzero(ok & (o["status"] == oracle.ST_OK))[0]:
+        if np.float32(o["score"][i]) != res["score"][i] or res["e_end"][i] != o["e_end"][i] or \
+                res["cells"][i] != o["cells"][i]:
+            bad.append((int(i), "result"))
+        elif not np.array_equal(gpu_pairs(pairs, po, res, i),
+                                o["pairs"][o["pair_off"][i]:o["pair_off"][i] + o["n_pairs"][i]]):
+            bad.append((int(i), "pairs"))
+    assert not bad, bad[:10]
