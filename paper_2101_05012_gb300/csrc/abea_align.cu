@@ -24,18 +24,19 @@
 //     [C*l, C*l + C) of every band; L = ceil(W/C) lanes are live.  The lanes
 //     above hold -inf scores and "no k-mer" operands (and an lp_skip of
 //     -inf), so they are the -inf edge of the band without any per-band test;
-//   - the previous two bands, the events and the k-mer operands of the
-//     lane's offsets live in registers.  A band move shifts either the k-mer
+//   - the previous band, the band before it (as the view the previous band
+//     read it through) and the events and k-mer operands of the lane's
+//     offsets live in registers.  A band move shifts either the k-mer
 //     operands (k-mer move) or the events (event move) by one offset; the one
 //     value that crosses a lane boundary travels by __shfl_*_sync.  The value
-//     entering at the band end comes from a warp-wide prefetch window (lane i
-//     holds the i-th next event / k-mer entry, the following 32 in flight);
-//   - the neighbours of a cell are a +-0/1 offset shift of the previous one
-//     or two bands, selected by the last two moves; the four cases are
-//     compiled separately so every register index is static;
+//     entering at the band end comes from a per-warp ring in shared memory,
+//     refilled by cp.async once per run of bands;
+//   - the neighbours of a cell are a +-0/1 offset shift of the previous band
+//     (left, up) and of the stored view of the band before it (diagonal),
+//     selected by the band's own move only; the two cases are compiled
+//     separately so every register index is static;
 //   - the move of band b+1 is decided at the end of band b (two shuffles of
-//     its end cells and a vote), so the decision overlaps band b's
-//     bookkeeping;
+//     its end cells), so the decision overlaps band b's bookkeeping;
 //   - the direction of every cell is two predicates (U over D; L over the
 //     max), gathered by __ballot_sync into 2C words per band and stored by
 //     the warp in one wide store (2 bits per cell); the band's move rides in
@@ -49,12 +50,14 @@
 //   - runs of bands whose W offsets all lie in the matrix go through a lean
 //     loop controlled by one counter (no trim, end or bound checks); the rest
 //     run the same step with those checks;
-//   - after the last band the same warp walks the trace back: the records of
-//     32 bands at a time are copied to shared memory with cp.async, two
-//     chunks ahead of the walk; each step reads its two trace words there and
-//     the band moves give each band's position; the pairs are gathered across
-//     the lanes and stored 32 at a time.
-//
+//   - after the last band the trace is walked back: the records of 32 bands
+//     at a time are copied to shared memory with cp.async, two chunks ahead
+//     of the walk; each step reads its two trace bits there and the band
+//     moves give each band's position.  A warp walks its reads two at a
+//     time, half a warp each, while the queue lasts (a read's walk waits for
+//     the warp's next read), and one at a time with the whole warp in the
+//     queue's tail.
+
 // All FP32 arithmetic uses explicitly rounded intrinsics, so no operation is
 // fused or reordered: the scores equal those of the FP32 canonical form,
 // in which every cell carries T = S + lp_step (S the recurrence's score):
@@ -1637,11 +1640,13 @@ struct Smem {
 
 // Persistent kernel.  Blocks 0 .. n_group-1 first align reads order[0 ..
 // n_group-1] in block mode (CG offsets per lane); then every warp takes reads
-// order[n_group ..] one at a time from the shared counter.
+// order[n_group ..] one at a time from the shared counter, and walks them two
+// at a time (walk2) or, in the queue's tail, one at a time (walk1).
 // Blocks per SM the register budget is set for: 5 where the band fits in at
 // most 96 registers without spilling much (C <= 2, and C = 4 with 25 lanes:
-// measured 3 % faster than 4 blocks at W = 100), 4 for the rest up to C = 5,
-// 3 for C >= 6 (168 registers; 10 % faster than 2 blocks at W = 200).
+// 5 ran 3 % faster than 4 blocks at W = 100; 6, 7 and 8 ran no faster or
+// spilled in the band loop), 4 for the rest up to C = 5, 3 for C >= 6
+// (168 registers; 10 % faster than 2 blocks at W = 200).
 template <int C, bool MIXED, bool FULLW>
 struct Occupancy {
     static constexpr int blocks = (C >= 6) ? 3 : (C <= 2 || (C == 4 && !MIXED && !FULLW)) ? 5 : 4;
