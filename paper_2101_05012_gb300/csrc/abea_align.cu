@@ -1023,7 +1023,7 @@ __device__ __noinline__ void walk1(int ja, int W, int bufs, int stages, abea_res
 // of slot i is Q[i + KM_b], so it is read at an index fixed by band b's own
 // move; S_b is written over H, and P becomes the next band's H: in place
 // after an event move (H = {P[0..C-1], boundary}), rotated by one register
-// after a k-mer move.  The band loop is unrolled by two (the two arrays
+// after a k-mer move.  The band loop is unrolled by four (the two arrays
 // alternate roles), with one branch per band on its move.  A compact loop
 // keeps the code of the hot path small enough for the instruction caches
 // (state machines over more than a handful of band variants ran slower,
