@@ -96,8 +96,9 @@ def test_ragged_lengths(ctx):
     compare(b, res, pairs, po)
 
 
-@pytest.mark.parametrize("W", [2, 3, 4, 5, 7, 16, 31, 32, 33, 50, 63, 64, 65, 100, 101, 127, 128, 129, 160, 200,
-                               201, 255, 256])
+# 30, 60, 120: two lanes above the band (L = 30); 31, 61, 62, 93, 121, 124: one lane above it (L = 31)
+@pytest.mark.parametrize("W", [2, 3, 4, 5, 7, 16, 30, 31, 32, 33, 50, 60, 61, 62, 63, 64, 65, 93, 100, 101, 120, 121,
+                               124, 127, 128, 129, 160, 200, 201, 255, 256])
 def test_band_widths(ctx, W):
     lengths = [6, 9, 30, 80, 150, 260, 420, 700]
     b = _lengths_batch(lengths, W=W, seed=W)
