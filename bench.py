@@ -66,7 +66,7 @@ UNIT = "GCUPS"
 OPS_PER_CELL = 14
 # DRAM bytes (read + write) per band of the core kernel from one ncu capture, valid only for the kernel
 # source it was taken on; scaled to a launch by the batch's bands.
-TRAFFIC_CAPTURE = {"source_sha1": "4a9988016ed60a0f69fde1c9c7ad93d930eeae30", "bytes_per_band": 85.326}
+TRAFFIC_CAPTURE = {"source_sha1": "798a3581a806576aed2c2f22486da0b330c3a50d", "bytes_per_band": 85.147}
 
 
 def parse():
