@@ -8,8 +8,9 @@ two calls in a row (the second call reuses the scratch array the first one
 left behind).  The cases reach every part of its own working-set layout: the
 4-word and 16-word records (W = 100, 200), the per-band move bytes (W = 128,
 all 32 lanes live), the largest model (k = 7), a read long enough for block
-mode, and a batch just under the 64 MiB working set.  This file is collected
-last.
+mode, 4,000 short reads (more than the launch has warps, so that most are
+walked two at a time) and a batch just under the 64 MiB working set.  This
+file is collected last.
 """
 import dataclasses
 
@@ -66,6 +67,10 @@ def _batch(case):
         return synth.make_batch(dataclasses.replace(synth.WORKLOADS["plain_64x1kb"], W=128), n_reads=32)
     if case == "w100_k7":
         return synth.make_batch(dataclasses.replace(synth.WORKLOADS["plain_64x1kb"], k=7), n_reads=32)
+    if case == "w100_k6_many_short":
+        # more reads than the launch has warps, so that most are walked two at a time
+        w = dataclasses.replace(synth.WORKLOADS["plain_64x1kb"], n_reads=4000, length=("fixed", 100))
+        return synth.make_batch(w)
     if case == "w200_k7_block":
         # one read far longer than the rest: it runs in block mode (default theta = 1)
         w = dataclasses.replace(synth.WORKLOADS["batch_4096_ln5kb"], k=7, W=200)
@@ -75,7 +80,7 @@ def _batch(case):
     raise ValueError(case)
 
 
-@pytest.mark.parametrize("case", ["w100_k6", "w200_k6", "w128_k6", "w100_k7", "w200_k7_block"])
+@pytest.mark.parametrize("case", ["w100_k6", "w200_k6", "w128_k6", "w100_k7", "w200_k7_block", "w100_k6_many_short"])
 def test_noalloc_matches_device_call_twice(case):
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
