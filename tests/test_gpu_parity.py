@@ -416,3 +416,15 @@ def test_paired_walks_with_rejected_and_short_slots(ctx):
                                 o["pairs"][o["pair_off"][i]:o["pair_off"][i] + o["n_pairs"][i]]):
             bad.append((int(i), "pairs"))
     assert not bad, bad[:10]
+
+
+def test_block_mode_then_paired_walks(ctx):
+    """A launch that starts with block-mode reads (the four longest, one per block) and then walks
+    the remaining 5,000 short reads mostly two at a time (warp 0 of those blocks reuses the region
+    its block-mode walk used): every read equals the FP32 oracle."""
+    rng = np.random.default_rng(23)
+    lengths = [9000, 8500, 8000, 7500] + rng.integers(120, 400, 5000).tolist()
+    b = _lengths_batch(lengths, seed=19)
+    res, pairs, po = run_gpu(ctx, b, theta=ALL_BLOCK)
+    assert np.all(res["status"] == 0)
+    compare(b, res, pairs, po, check_f64=False)
