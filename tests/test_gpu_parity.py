@@ -428,3 +428,29 @@ def test_block_mode_then_paired_walks(ctx):
     res, pairs, po = run_gpu(ctx, b, theta=ALL_BLOCK)
     assert np.all(res["status"] == 0)
     compare(b, res, pairs, po, check_f64=False)
+
+
+# (events, bases) of reads whose band leaves the matrix early on one side, and tiny near-square ones
+DEGENERATE_SHAPES = [(1, 6), (1, 7), (1, 60), (1, 400), (2, 6), (2, 105), (3, 300), (3, 1000), (40, 6),
+                     (500, 6), (2000, 7), (150, 8), (5, 5000), (7, 7), (8, 13), (120, 110)]
+
+
+def _degenerate_batch(k=6, W=100, seed=41):
+    mm, ms = synth.make_model(k, 31)
+    rng = np.random.default_rng(seed)
+    events, seqs, sc = [], [], []
+    for n_e, L in DEGENERATE_SHAPES:
+        seqs.append(rng.choice(np.frombuffer(b"ACGT", np.uint8), L).tobytes())
+        events.append(rng.uniform(60.0, 130.0, n_e).astype(np.float32))
+        sc.append((1.0, 0.0, 1.0))
+    return synth.custom_batch(events, seqs, sc, mm, ms, k, W)
+
+
+@pytest.mark.parametrize("theta", [1.0, ALL_BLOCK])
+def test_degenerate_shapes(ctx, theta):
+    """One to three events against up to 5,000 bases, one or two k-mers against up to 2,000 events,
+    and tiny near-square reads, per warp and in block mode: status, end event, cells, pairs and
+    score equal the FP32 oracle's on every read."""
+    b = _degenerate_batch()
+    res, pairs, po = run_gpu(ctx, b, theta=theta)
+    compare(b, res, pairs, po)
