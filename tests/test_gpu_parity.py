@@ -454,3 +454,47 @@ def test_degenerate_shapes(ctx, theta):
     b = _degenerate_batch()
     res, pairs, po = run_gpu(ctx, b, theta=theta)
     compare(b, res, pairs, po)
+
+
+@pytest.mark.parametrize("theta", [1.0, ALL_BLOCK])
+def test_page_locked_host_buffers(ctx, theta):
+    """abea_align_packed with page-locked host arrays takes the direct path (copies straight to and
+    from the caller's arrays, no staging on the host).  Results and every aligned read's pairs equal
+    the pageable call's and the FP32 oracle's, with spare capacity in the slots and a read one pair
+    short of its alignment (status CAPACITY with the required count), per warp and in block mode."""
+    torch = pytest.importorskip("torch")
+    b = _lengths_batch([200, 400, 600, 5000, 30, 12000, 80, 2500], seed=12)
+    o = oracle.abea_batch(b, "f32", n_threads=THREADS)
+    need = o["n_pairs"].astype(np.int64)
+    caps = need + 7
+    caps[1] = need[1] - 1                          # one pair short
+    po = np.zeros(b.n + 1, np.int64)
+    np.cumsum(caps, out=po[1:])
+    ref_res, ref_pairs, _ = run_gpu(ctx, b, pair_off=po, theta=theta)
+    assert ref_res["status"][1] == binding.READ_CAPACITY and ref_res["n_pairs"][1] == need[1]
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    seq, ev = pin(b.seq), pin(b.events)
+    out = pin(np.zeros(b.n * 24, np.uint8))
+    pairs = pin(np.full(int(po[-1]) * 2, -7, np.int32))
+    sc = np.ascontiguousarray(b.scalings, np.float32)
+    ctx.set_model(b.k, b.model_mean, b.model_stdv)
+    ctx.set_block_mode(theta)
+    try:
+        rc = ctx.lib.abea_align_packed(ctx.h, b.n, b.W, binding._p(seq), binding._p(b.seq_off), binding._p(ev),
+                                       binding._p(b.ev_off), binding._p(sc), binding._p(out), binding._p(pairs),
+                                       binding._p(po), None)
+    finally:
+        ctx.set_block_mode(1.0)
+    assert rc == 0
+    res = binding.results_from_bytes(out)
+    assert np.array_equal(res, ref_res)
+    pairs = pairs.reshape(-1, 2)
+    for i in range(b.n):
+        if res["status"][i] != binding.READ_OK:
+            continue
+        lo, m = int(po[i]), int(res["n_pairs"][i])
+        assert np.array_equal(pairs[lo:lo + m], ref_pairs[lo:lo + m])
+        assert np.array_equal(pairs[lo:lo + m], o["pairs"][o["pair_off"][i]:o["pair_off"][i] + m])
